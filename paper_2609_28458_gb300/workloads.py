@@ -1,0 +1,176 @@
+"""Seeded synthetic ensembles for the four workloads (inputs only; no integration arithmetic).
+
+Each generator returns NumPy FP64 arrays: y0 [N, d], params [N, p], t0 [N], t1 [N], saveat [K]
+(or [N, K]), plus the tolerances and method the workload is run with. The same arrays feed the
+GPU library and the CPU oracle; neither side's arithmetic lives here. Seeds follow
+``seed = workload index * 1000 + repetition``.
+
+Workloads (shapes and distributions of the paper's ensembles, Sec. 3-5, with the potentials and
+sizes of the benchmark configurations):
+
+* ``isochrone``: test particles in Phi = -1/(1+sqrt(1+r^2)) (G = M = b = 1); r ~ U[0.5, 5],
+  isotropic position and velocity directions, speed U[0.3, 0.9] x v_circ(r); t in [0, 100],
+  11 equally spaced outputs; Tsit5, rtol 1e-10, atol 1e-12.
+* ``mw``: Milky-Way-like potential (Miyamoto-Nagai disc + Hernquist bulge + flattened NFW halo),
+  units kpc, Myr, 1e10 Msun; R ~ U[4, 20] kpc, phi ~ U[0, 2pi), z ~ U[-2, 2] kpc, velocity
+  v_circ(R, 0) phi-hat plus N(0, (20 km/s)^2) per component; q_halo ~ U[0.8, 1.2];
+  t in [0, 3000] Myr, endpoint output; Tsit5, rtol = atol = 3e-7.
+* ``precession``: binary black holes, M ~ U[10, 100] Msun, q ~ U[0.1, 1], chi_j ~ U[0, 1],
+  isotropic spin directions, Lhat = z-hat; integrated in v from the 20 Hz gravitational-wave
+  frequency to v = 0.3 (or, paper-faithful, from r = 100 M to 10 M); endpoint output.
+* ``quintessence``: lambda ~ U[0, 1.5], Omega_m ~ U[0.28, 0.34], Omega_r = 9e-5, amplitude
+  a0 = 1 - Omega_m - Omega_r (supplied); field at rest at z = 50; outputs at 7 redshifts spread
+  uniformly in ln(1+z) over [0.3, 2.4] plus today (or 64 nodes over [0, 3]); rtol 1e-4..1e-6,
+  atol = 1e-3 rtol.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# units: kpc, Myr, 1e10 Msun. G from GM_sun = 1.3271244e20 m^3/s^2, kpc = 3.0856775814913673e19 m,
+# Myr = 3.15576e13 s.
+_GM_SUN, _KPC, _MYR = 1.3271244e20, 3.0856775814913673e19, 3.15576e13
+G_KPC_MYR = 1e10 * _GM_SUN * _MYR * _MYR / (_KPC ** 3)
+KMS_IN_KPC_MYR = 1e3 * _MYR / _KPC
+MW_PARAMS = (6.8, 0.5, 54.0, 1.0)  # (M_disc, M_bulge, M_halo in 1e10 Msun, q_halo)
+MW_SCALES = dict(a=3.0, b=0.28, c=1.0, rs=15.6)
+T_SUN_S = 4.925490947641267e-6  # G Msun / c^3 in seconds
+
+
+@dataclass
+class Ensemble:
+    system: str
+    y0: np.ndarray
+    params: np.ndarray
+    t0: np.ndarray
+    t1: np.ndarray
+    saveat: np.ndarray
+    rtol: float
+    atol: float
+    method: str = "tsit5"
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return self.y0.shape[0]
+
+    def subset(self, idx):
+        idx = np.asarray(idx)
+        sv = self.saveat[idx] if self.saveat.ndim == 2 else self.saveat
+        return Ensemble(self.system, self.y0[idx].copy(), self.params[idx].copy(), self.t0[idx].copy(),
+                        self.t1[idx].copy(), sv.copy(), self.rtol, self.atol, self.method, dict(self.extra))
+
+
+def _isotropic(rng, n):
+    u = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2 * np.pi, n)
+    s = np.sqrt(1.0 - u * u)
+    return np.stack([s * np.cos(ph), s * np.sin(ph), u], axis=1)
+
+
+def isochrone(n=4096, seed=0):
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.5, 5.0, n)
+    xhat = _isotropic(rng, n)
+    s = np.sqrt(1.0 + r * r)
+    vcirc = np.sqrt(r * r / ((1.0 + s) ** 2 * s))
+    speed = rng.uniform(0.3, 0.9, n) * vcirc
+    vhat = _isotropic(rng, n)
+    y0 = np.concatenate([xhat * r[:, None], vhat * speed[:, None]], axis=1)
+    return Ensemble("isochrone", y0, np.zeros((n, 0)), np.zeros(n), np.full(n, 100.0),
+                    np.linspace(0.0, 100.0, 11), 1e-10, 1e-12, "tsit5")
+
+
+def mw_vcirc(R, params=MW_PARAMS):
+    """Circular speed in the plane z = 0 from the radial forces of the three components."""
+    G = G_KPC_MYR
+    a, b, c, rs = MW_SCALES["a"], MW_SCALES["b"], MW_SCALES["c"], MW_SCALES["rs"]
+    md, mb, mh = params[0], params[1], params[2]
+    dphi_disc = G * md * R / (R * R + (a + b) ** 2) ** 1.5
+    dphi_bulge = G * mb / (R + c) ** 2
+    dphi_halo = G * mh * (np.log1p(R / rs) / R ** 2 - 1.0 / (R * (rs + R)))
+    return np.sqrt(R * (dphi_disc + dphi_bulge + dphi_halo))
+
+
+def mw(n=1 << 20, seed=1000, t1=3000.0, rtol=3e-7):
+    rng = np.random.default_rng(seed)
+    R = rng.uniform(4.0, 20.0, n)
+    ph = rng.uniform(0.0, 2 * np.pi, n)
+    z = rng.uniform(-2.0, 2.0, n)
+    vc = mw_vcirc(R)
+    sig = 20.0 * KMS_IN_KPC_MYR
+    dv = rng.normal(0.0, sig, (n, 3))
+    x = np.stack([R * np.cos(ph), R * np.sin(ph), z], axis=1)
+    v = np.stack([-vc * np.sin(ph), vc * np.cos(ph), np.zeros(n)], axis=1) + dv
+    q = rng.uniform(0.8, 1.2, n)
+    params = np.tile(np.array(MW_PARAMS[:3]), (n, 1))
+    params = np.concatenate([params, q[:, None]], axis=1)
+    return Ensemble("mw", np.concatenate([x, v], axis=1), params, np.zeros(n), np.full(n, t1),
+                    np.array([t1]), rtol, rtol, "tsit5")
+
+
+def precession(n=1_000_000, seed=2000, method="vern7", rtol=None, paper_interval=False):
+    rng = np.random.default_rng(seed)
+    M = rng.uniform(10.0, 100.0, n)
+    q = rng.uniform(0.1, 1.0, n)
+    chi1 = rng.uniform(0.0, 1.0, n)
+    chi2 = rng.uniform(0.0, 1.0, n)
+    c1 = rng.uniform(-1.0, 1.0, n)
+    c2 = rng.uniform(-1.0, 1.0, n)
+    dphi = rng.uniform(0.0, 2 * np.pi, n)
+    s1, s2 = np.sqrt(1 - c1 * c1), np.sqrt(1 - c2 * c2)
+    L = np.tile(np.array([0.0, 0.0, 1.0]), (n, 1))
+    S1 = np.stack([s1, np.zeros(n), c1], axis=1)
+    S2 = np.stack([s2 * np.cos(dphi), s2 * np.sin(dphi), c2], axis=1)
+    y0 = np.concatenate([L, S1, S2], axis=1)
+    params = np.stack([q, chi1, chi2], axis=1)
+    if paper_interval:
+        t0 = np.full(n, 0.1)
+        t1v = 10.0 ** -0.5
+    else:
+        # v = (pi M T_sun f)^(1/3) at gravitational-wave frequency f = 20 Hz
+        t0 = (np.pi * M * T_SUN_S * 20.0) ** (1.0 / 3.0)
+        t1v = 0.3
+    if rtol is None:
+        rtol = 3.16e-9 if method == "vern7" else 5.62e-10
+    return Ensemble("precession", y0, params, t0, np.full(n, t1v), np.array([t1v]), rtol, rtol, method,
+                    dict(M=M))
+
+
+def quintessence_redshifts(dense=False):
+    if dense:
+        return np.expm1(np.linspace(0.0, np.log(4.0), 64))
+    return np.expm1(np.linspace(np.log(1.3), np.log(3.4), 7))
+
+
+def quintessence(n=10_000, seed=3000, rtol=1e-6, method="tsit5", dense=False, omega_r=9e-5):
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(0.0, 1.5, n)
+    om = rng.uniform(0.28, 0.34, n)
+    a0 = 1.0 - om - omega_r
+    params = np.stack([a0, lam, om, np.full(n, omega_r)], axis=1)
+    z = quintessence_redshifts(dense)
+    Nz = np.sort(-np.log1p(z))
+    saveat = np.unique(np.concatenate([Nz, [0.0]]))
+    return Ensemble("quintessence", np.zeros((n, 3)), params, np.full(n, -np.log(51.0)), np.zeros(n), saveat,
+                    rtol, 1e-3 * rtol, method, dict(z=z))
+
+
+def loghalo(n=10_000, seed=4000, rtol=3.16e-7):
+    """Flattened logarithmic halo of Sec. 3 with (v_c, R_c, q) = (1, 0.2, 0.7): orbits started in
+    and out of the plane, from near-circular to nearly radial, run for about four periods."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.5, 2.0, n)
+    xhat = _isotropic(rng, n)
+    speed = rng.uniform(0.3, 1.0, n)
+    vhat = _isotropic(rng, n)
+    y0 = np.concatenate([xhat * r[:, None], vhat * speed[:, None]], axis=1)
+    period = 2 * np.pi * r
+    params = np.tile(np.array([1.0, 0.2, 0.7]), (n, 1))
+    t1 = 3.7 * period
+    return Ensemble("loghalo", y0, params, np.zeros(n), t1, t1[:, None].copy(), rtol, rtol, "tsit5")
+
+
+def by_name(name, **kw):
+    return dict(isochrone=isochrone, mw=mw, precession=precession, quintessence=quintessence,
+                loghalo=loghalo)[name](**kw)

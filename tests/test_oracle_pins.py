@@ -1,0 +1,405 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (CPU only).
+
+* isochrone closed forms: radial period T_r = 2 pi / (-2E)^(3/2) and azimuth advance per radial
+  period pi (1 + L / sqrt(L^2 + 4)) (Binney & Tremaine, the textbook the paper cites in Sec. 3);
+  apocentre radius at T_r / 2 from the radial energy equation;
+* measured convergence orders of every tableau and of the dense output on that closed form;
+* conserved quantities: energy and angular momentum of the orbit systems (Sec. 3); unit lengths,
+  effective spin and total angular momentum of the precession equations (Sec. 5); Lambda-CDM
+  distances by Gauss-Legendre quadrature at lambda = 0, and the decrease of rho_phi (Eq. de-rho)
+  and w >= -1 (Eq. de-w) for lambda > 0 (Sec. 4, Appendix C);
+* the exactness statement of Sec. 2.3 / Eq. stage-sens: forward sensitivities on a fixed step
+  sequence equal the derivative of the discrete solution (central differences of the replay);
+* the converged-reference check of Appendix A / Appendix D (10x looser tolerance within eps_req/10);
+* the failure conventions (status codes, NaN outputs).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_28458_gb300 import metrics as M
+from paper_2609_28458_gb300 import workloads as W
+
+
+def _iso_elements(y0):
+    x, v = y0[:, :3], y0[:, 3:]
+    r0 = np.linalg.norm(x, axis=1)
+    E = 0.5 * (v ** 2).sum(1) - 1.0 / (1.0 + np.sqrt(1.0 + r0 ** 2))
+    Lv = np.cross(x, v)
+    L = np.linalg.norm(Lv, axis=1)
+    Tr = 2 * np.pi / (-2 * E) ** 1.5
+    dpsi = np.pi * (1 + L / np.sqrt(L ** 2 + 4))
+    return r0, E, Lv, L, Tr, dpsi
+
+
+def _azimuth(x0, x1, Lv):
+    nh = Lv / np.linalg.norm(Lv, axis=1)[:, None]
+    return np.arctan2((nh * np.cross(x0, x1)).sum(1), (x0 * x1).sum(1))
+
+
+def _wrap(a):
+    return np.abs(np.mod(a + np.pi, 2 * np.pi) - np.pi)
+
+
+# ---------------------------------------------------------------------------------------------
+def test_isochrone_radial_period_and_azimuth_converged():
+    e = W.isochrone(n=32, seed=7)
+    r0, E, Lv, L, Tr, dpsi = _iso_elements(e.y0)
+    res = O.solve("isochrone", e.y0, None, 0.0, Tr, Tr[:, None], 1e-13, 1e-13, method="vern7")
+    assert np.all(res["status"] == 0)
+    y = res["y"][:, 0]
+    r1 = np.linalg.norm(y[:, :3], axis=1)
+    assert np.max(np.abs(r1 - r0) / r0) < 1e-11
+    ang = _azimuth(e.y0[:, :3], y[:, :3], Lv)
+    assert np.max(_wrap(ang - dpsi)) < 1e-10
+
+
+@pytest.mark.parametrize("method", ["tsit5", "dopri5"])
+def test_isochrone_same_algorithm_at_workload_tolerance(method):
+    e = W.isochrone(n=32, seed=8)
+    r0, E, Lv, L, Tr, dpsi = _iso_elements(e.y0)
+    res = O.solve("isochrone", e.y0, None, 0.0, Tr, Tr[:, None], 1e-10, 1e-12, method=method)
+    r1 = np.linalg.norm(res["y"][:, 0, :3], axis=1)
+    assert np.max(np.abs(r1 - r0) / r0) < 3e-9
+
+
+def _pericentre_orbit():
+    # start at pericentre: x = (r_p, 0, 0), v = (0, v_t, 0) with v_t above the circular speed
+    rp = 1.0
+    s = np.sqrt(1 + rp * rp)
+    vc = np.sqrt(rp * rp / ((1 + s) ** 2 * s))
+    y0 = np.array([[rp, 0.0, 0.0, 0.0, 1.3 * vc, 0.0]])
+    r0, E, Lv, L, Tr, dpsi = _iso_elements(y0)
+    # apocentre: other root of E = L^2/(2 r^2) + Phi(r)
+    g = lambda r: 0.5 * L[0] ** 2 / r ** 2 - 1.0 / (1.0 + np.sqrt(1.0 + r * r)) - E[0]
+    lo, hi = 1.01 * rp, 100.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if g(mid) < 0:
+            lo = mid
+        else:
+            hi = mid
+    return y0, Tr[0], 0.5 * (lo + hi)
+
+
+def _uniform_tape(T, n):
+    return np.full((1, n), T / n), np.array([n], np.int32)
+
+
+@pytest.mark.parametrize("method,nu,ns", [("tsit5", 5, (40, 80, 160)), ("dopri5", 5, (40, 80, 160)),
+                                          ("vern7", 7, (20, 40, 80))])
+def test_convergence_order_on_closed_form(method, nu, ns):
+    """Fixed steps over one radial period: |r(T_r) - r0| must shrink as h^nu."""
+    y0, Tr, _ = _pericentre_orbit()
+    errs = []
+    for n in ns:
+        tape, nt = _uniform_tape(Tr, n)
+        y = O.replay("isochrone", y0, None, 0.0, Tr, np.array([Tr]), tape, nt, method=method)
+        errs.append(abs(np.linalg.norm(y[0, 0, :3]) - 1.0))
+    slopes = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(abs(s - nu) < 0.6 for s in slopes), (errs, slopes)
+
+
+@pytest.mark.parametrize("method", ["tsit5", "dopri5"])
+def test_dense_output_convergence_on_closed_form(method):
+    """Output at T_r/2 (apocentre) falls strictly inside a step for odd step counts; the dense
+    solution must converge to the apocentre radius at order >= 4.5 (Eq. dense)."""
+    y0, Tr, rapo = _pericentre_orbit()
+    errs = []
+    for n in (41, 81, 161):
+        tape, nt = _uniform_tape(Tr, n)
+        y = O.replay("isochrone", y0, None, 0.0, Tr, np.array([0.5 * Tr]), tape, nt, method=method)
+        errs.append(abs(np.linalg.norm(y[0, 0, :3]) - rapo))
+    slopes = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(slopes) > 4.5, (errs, slopes)
+
+
+def test_vern7_shortened_step_output_converges():
+    y0, Tr, rapo = _pericentre_orbit()
+    res = O.solve("isochrone", y0, None, 0.0, Tr, np.array([0.5 * Tr, Tr]), 1e-12, 1e-12, method="vern7")
+    assert abs(np.linalg.norm(res["y"][0, 0, :3]) - rapo) < 1e-10
+
+
+@pytest.mark.parametrize("method,nu", [("tsit5", 5), ("vern7", 7)])
+def test_step_count_scales_with_tolerance(method, nu):
+    """With error-per-step control by an embedded pair of orders (nu, nu-1) the step length scales
+    as tol^(1/nu): the accepted-step count over four decades of rtol must grow as 10^(4/nu)."""
+    e = W.isochrone(n=16, seed=9)
+    counts = []
+    for rtol in (1e-6, 1e-10):
+        res = O.solve("isochrone", e.y0, None, 0.0, 100.0, np.array([100.0]), rtol, rtol, method=method)
+        counts.append(res["n_accept"].mean())
+    slope = np.log10(counts[1] / counts[0]) / 4.0
+    assert abs(slope - 1.0 / nu) < 0.04, (counts, slope)
+
+
+# ---------------------------------------------------------------------------------------------
+def _energy(system, y, params):
+    return 0.5 * (y[..., 3:] ** 2).sum(-1) + M.potential(system, y[:, :3], params)
+
+
+@pytest.mark.parametrize("system,gen", [("isochrone", lambda: W.isochrone(n=16, seed=3)),
+                                        ("mw", lambda: W.mw(n=16, seed=3, t1=1000.0)),
+                                        ("loghalo", lambda: W.loghalo(n=16, seed=3))])
+def test_orbit_invariants(system, gen):
+    e = gen()
+    res = O.solve(system, e.y0, e.params, e.t0, e.t1, e.saveat, 1e-12, 1e-12)
+    assert np.all(res["status"] == 0)
+    y1 = res["y"][:, -1]
+    E0 = _energy(system, e.y0, e.params)
+    E1 = _energy(system, y1, e.params)
+    assert np.max(np.abs(E1 - E0) / np.abs(E0)) < 1e-9
+    Lz0 = e.y0[:, 0] * e.y0[:, 4] - e.y0[:, 1] * e.y0[:, 3]
+    Lz1 = y1[:, 0] * y1[:, 4] - y1[:, 1] * y1[:, 3]
+    Lscale = np.linalg.norm(np.cross(e.y0[:, :3], e.y0[:, 3:]), axis=1)
+    assert np.max(np.abs(Lz1 - Lz0) / Lscale) < 1e-9
+    # energy drift must be of the size the tolerance implies, not zero: the solve did integrate
+    assert np.max(np.linalg.norm(y1[:, :3] - e.y0[:, :3], axis=1)) > 1e-3
+    if system == "isochrone":  # spherical: the full angular momentum vector
+        L1 = np.cross(y1[:, :3], y1[:, 3:])
+        L0 = np.cross(e.y0[:, :3], e.y0[:, 3:])
+        assert np.max(np.linalg.norm(L1 - L0, axis=1) / Lscale) < 1e-9
+
+
+def test_mw_spherical_halo_conserves_full_angular_momentum_without_disc():
+    e = W.mw(n=8, seed=4, t1=500.0)
+    p = e.params.copy()
+    p[:, 0] = 0.0  # no disc
+    p[:, 3] = 1.0  # spherical halo
+    res = O.solve("mw", e.y0, p, e.t0, e.t1, e.saveat, 1e-12, 1e-12)
+    y1 = res["y"][:, -1]
+    L0 = np.cross(e.y0[:, :3], e.y0[:, 3:])
+    L1 = np.cross(y1[:, :3], y1[:, 3:])
+    assert np.max(np.linalg.norm(L1 - L0, axis=1) / np.linalg.norm(L0, axis=1)) < 1e-9
+
+
+def test_orbit_rhs_is_minus_gradient_of_potential():
+    """The acceleration equals minus the central-difference gradient of Phi (Eq. loghalo)."""
+    rng = np.random.default_rng(0)
+    for system, p in (("isochrone", np.zeros(4)), ("mw", np.array([6.8, 0.5, 54.0, 0.9])),
+                      ("loghalo", np.array([1.0, 0.2, 0.7]))):
+        for _ in range(5):
+            x = rng.uniform(-5, 5, 3)
+            f = O.rhs(system, 0.0, np.concatenate([x, [0.1, 0.2, 0.3]]), p)
+            assert np.allclose(f[:3], [0.1, 0.2, 0.3], rtol=0, atol=0)
+            g = np.zeros(3)
+            for i in range(3):
+                dx = np.zeros(3)
+                dx[i] = 1e-5
+                g[i] = (O.potential(system, x + dx, p) - O.potential(system, x - dx, p)) / 2e-5
+            assert np.allclose(f[3:], -g, rtol=1e-7, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+def _prec_quantities(y, p):
+    q, chi1, chi2 = p[..., 0], p[..., 1], p[..., 2]
+    m1, m2 = 1 / (1 + q), q / (1 + q)
+    S1, S2 = chi1 * m1 ** 2, chi2 * m2 ** 2
+    L, s1, s2 = y[..., 0:3], y[..., 3:6], y[..., 6:9]
+    xi = ((1 + q) * S1)[..., None] * s1 + ((1 + 1 / q) * S2)[..., None] * s2
+    return L, s1, s2, (xi * L).sum(-1), S1, S2, m1 * m2
+
+
+def test_precession_rhs_identities():
+    """At random states: |Lhat|, |S_jhat| fixed (Eq. prec-spins, prec-L), effective spin fixed, and
+    the total angular momentum J = (eta/v) Lhat + S1 + S2 changes only through L: dJ/dv = -eta/v^2 Lhat
+    (Sec. 5: Eq. prec-L keeps L + S1 + S2 fixed on the precession time-scale)."""
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        v = rng.uniform(0.05, 0.4)
+        p = np.array([rng.uniform(0.1, 1.0), rng.uniform(0, 1), rng.uniform(0, 1)])
+        vecs = [u / np.linalg.norm(u) for u in rng.normal(size=(3, 3))]
+        y = np.concatenate(vecs)
+        f = O.rhs("precession", v, y, p)
+        L, s1, s2, xi, S1, S2, eta = _prec_quantities(y, p)
+        fL, f1, f2 = f[0:3], f[3:6], f[6:9]
+        scale = np.abs(f).max()
+        assert abs(L @ fL) < 1e-13 * scale and abs(s1 @ f1) < 1e-13 * scale and abs(s2 @ f2) < 1e-13 * scale
+        q = p[0]
+        dxi = (1 + q) * S1 * (f1 @ L + s1 @ fL) + (1 + 1 / q) * S2 * (f2 @ L + s2 @ fL)
+        assert abs(dxi) < 1e-13 * scale
+        dJ = (eta / v) * fL + S1 * f1 + S2 * f2  # dJ/dv + eta/v^2 Lhat
+        assert np.max(np.abs(dJ)) < 1e-13 * scale * max(S1 + S2 + eta / v, 1.0)
+
+
+def test_precession_solve_invariants():
+    e = W.precession(n=16, seed=5, paper_interval=True)
+    res = O.solve("precession", e.y0, e.params, e.t0, e.t1, e.saveat, 1e-11, 1e-11, method="vern7")
+    assert np.all(res["status"] == 0)
+    y1 = res["y"][:, -1]
+    for j in range(3):
+        assert np.max(np.abs(np.linalg.norm(y1[:, 3 * j:3 * j + 3], axis=1) - 1.0)) < 1e-8
+    xi0 = _prec_quantities(e.y0, e.params)[3]
+    xi1 = _prec_quantities(y1, e.params)[3]
+    assert np.max(np.abs(xi1 - xi0)) < 1e-8
+    # and the spins did precess
+    assert np.max(np.linalg.norm(y1[:, 3:6] - e.y0[:, 3:6], axis=1)) > 1e-2
+
+
+def test_precession_empty_interval_above_87_msun():
+    e = W.precession(n=64, seed=6)
+    res = O.solve("precession", e.y0, e.params, e.t0, e.t1, e.saveat, 1e-9, 1e-9, method="vern7")
+    empty = e.extra["M"] > 0.3 ** 3 / (np.pi * W.T_SUN_S * 20.0)
+    assert np.array_equal(res["status"] == O.ST_EMPTY_INTERVAL, empty)
+    assert np.array_equal(res["y"][empty, 0], e.y0[empty])
+    assert np.all(res["n_accept"][empty] == 0)
+
+
+# ---------------------------------------------------------------------------------------------
+def _gauss_legendre_DM(z, om, orad, a0, n=200):
+    x, w = np.polynomial.legendre.leggauss(n)
+    zz = 0.5 * z * (x + 1)
+    E = np.sqrt(om * (1 + zz) ** 3 + orad * (1 + zz) ** 4 + a0)
+    return 0.5 * z * np.sum(w / E)
+
+
+def test_quintessence_lambda_zero_is_lcdm():
+    e = W.quintessence(n=8, seed=1)
+    p = e.params.copy()
+    p[:, 1] = 0.0
+    res = O.solve("quintessence", e.y0, p, e.t0, e.t1, e.saveat, 1e-11, 1e-13)
+    y = res["y"]
+    assert np.all(y[:, :, 0] == 0.0) and np.all(y[:, :, 1] == 0.0)  # field never moves
+    DM, DH = M.distances(y, p, e.saveat)
+    z = np.expm1(-e.saveat[:-1])
+    for n in range(8):
+        a0, lam, om, orad = p[n]
+        ref = np.array([_gauss_legendre_DM(zz, om, orad, a0) for zz in z])
+        assert np.max(np.abs(DM[n] - ref)) < 1e-9
+        Eref = np.sqrt(om * (1 + z) ** 3 + orad * (1 + z) ** 4 + a0)
+        assert np.max(np.abs(DH[n] - 1 / Eref)) < 1e-13
+
+
+def test_quintessence_rho_phi_decreases_and_w_above_minus_one():
+    e = W.quintessence(n=16, seed=2, dense=True)
+    p = e.params.copy()
+    p[:, 1] = np.linspace(0.2, 1.5, 16)
+    res = O.solve("quintessence", e.y0, p, e.t0, e.t1, e.saveat, 1e-10, 1e-13)
+    y = res["y"]
+    E = M.quintessence_E(e.saveat[None, :], y, p)
+    kin = E ** 2 * y[:, :, 1] ** 2 / 6
+    pot = p[:, 0:1] * np.exp(-p[:, 1:2] * y[:, :, 0])
+    rho = kin + pot
+    assert np.all(np.diff(rho, axis=1) <= 1e-14)
+    w = (kin - pot) / (kin + pot)
+    assert np.all(w >= -1.0) and np.all(w[:, -1] > -1.0)
+    assert np.all(y[:, -1, 1] > 0)  # the field has started to roll
+
+
+# ---------------------------------------------------------------------------------------------
+def _fd_loss(system, e, w, tape, nt, method, dy0=None, dp=None):
+    y0 = e.y0 + (dy0 if dy0 is not None else 0)
+    pp = e.params + (dp if dp is not None else 0)
+    y = O.replay(system, y0, pp, e.t0, e.t1, e.saveat, tape, nt, method=method)
+    return np.sum(w * y, axis=(1, 2))
+
+
+@pytest.mark.parametrize("system,gen,method", [
+    ("mw", lambda: W.mw(n=4, seed=11, t1=300.0), "tsit5"),
+    ("precession", lambda: W.precession(n=4, seed=12, paper_interval=True), "vern7"),
+    ("quintessence", lambda: W.quintessence(n=4, seed=13), "dopri5"),
+    ("loghalo", lambda: W.loghalo(n=4, seed=14), "tsit5"),
+])
+def test_sensitivities_are_exact_derivative_of_discrete_solution(system, gen, method):
+    """Sec. 2.3 / Eq. stage-sens: on a fixed step sequence the forward sensitivities equal the
+    derivative of the numerical solution; checked against central differences of the replay."""
+    e = gen()
+    rec = O.solve(system, e.y0, e.params, e.t0, e.t1, e.saveat, 1e-7, 1e-7, method=method, record=True)
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=rec["y"].shape)
+    g = O.grad(system, e.y0, e.params, e.t0, e.t1, e.saveat, w, method=method, tape=rec["tape"],
+               ntape=rec["ntape"])
+    # the replay reproduces the adaptive solution bit for bit
+    yr = O.replay(system, e.y0, e.params, e.t0, e.t1, e.saveat, rec["tape"], rec["ntape"], method=method)
+    assert np.array_equal(yr, rec["y"])
+    assert np.array_equal(g["y"], rec["y"])
+    d, np_ = O.dims(system)
+    for i in range(d):
+        eps = 1e-6 * max(1.0, np.abs(e.y0[:, i]).max())
+        dy = np.zeros_like(e.y0)
+        dy[:, i] = eps
+        fd = (_fd_loss(system, e, w, rec["tape"], rec["ntape"], method, dy0=dy) -
+              _fd_loss(system, e, w, rec["tape"], rec["ntape"], method, dy0=-dy)) / (2 * eps)
+        assert np.allclose(g["dLdy0"][:, i], fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max() + 1e-12), (i, g["dLdy0"][:, i], fd)
+    for k in range(np_):
+        eps = 1e-6 * max(1.0, np.abs(e.params[:, k]).max())
+        dp = np.zeros_like(e.params)
+        dp[:, k] = eps
+        fd = (_fd_loss(system, e, w, rec["tape"], rec["ntape"], method, dp=dp) -
+              _fd_loss(system, e, w, rec["tape"], rec["ntape"], method, dp=-dp)) / (2 * eps)
+        assert np.allclose(g["dLdparams"][:, k], fd, rtol=1e-5, atol=1e-7 * np.abs(fd).max() + 1e-12), (k, g["dLdparams"][:, k], fd)
+
+
+def test_sensitivities_agree_with_differences_of_adaptive_solve():
+    """The derivative of the discrete solution approximates that of the exact flow to about the
+    tolerance level: central differences of the full adaptive solve at tight tolerance."""
+    e = W.mw(n=3, seed=15, t1=300.0)
+    w = np.random.default_rng(1).normal(size=(3, 1, 6))
+    g = O.grad("mw", e.y0, e.params, e.t0, e.t1, e.saveat, w, rtol=1e-11, atol=1e-11)
+    for k in range(4):
+        eps = 1e-4 * abs(e.params[0, k])
+        dp = np.zeros_like(e.params)
+        dp[:, k] = eps
+        lp = np.sum(w * O.solve("mw", e.y0, e.params + dp, e.t0, e.t1, e.saveat, 1e-12, 1e-12)["y"], axis=(1, 2))
+        lm = np.sum(w * O.solve("mw", e.y0, e.params - dp, e.t0, e.t1, e.saveat, 1e-12, 1e-12)["y"], axis=(1, 2))
+        fd = (lp - lm) / (2 * eps)
+        assert np.allclose(g["dLdparams"][:, k], fd, rtol=1e-4, atol=1e-6 * np.abs(fd).max())
+
+
+def test_jvp_matches_central_difference_of_rhs():
+    rng = np.random.default_rng(2)
+    cases = [("isochrone", 6, 0), ("mw", 6, 4), ("precession", 9, 3), ("quintessence", 3, 4), ("loghalo", 6, 3)]
+    base_p = {"mw": [6.8, 0.5, 54.0, 0.9], "precession": [0.5, 0.7, 0.3], "quintessence": [0.7, 0.8, 0.3, 9e-5],
+              "loghalo": [1.0, 0.2, 0.7], "isochrone": [0.0]}
+    for system, d, np_ in cases:
+        t = {"precession": 0.2, "quintessence": -1.0}.get(system, 0.0)
+        y = rng.uniform(-1, 1, d) + (np.array([3, 4, 1, 0, 0, 0]) if d == 6 else 0)
+        if system == "precession":
+            y = np.concatenate([u / np.linalg.norm(u) for u in rng.normal(size=(3, 3))])
+        if system == "quintessence":
+            y = np.array([0.3, 0.5, 1.0])
+        p = np.array(base_p[system], dtype=float)
+        vy, vp = rng.normal(size=d), rng.normal(size=max(np_, 1))
+        j = O.jvp(system, t, y, p, vy, vp if np_ else None)
+        eps = 1e-6
+        fp = O.rhs(system, t, y + eps * vy, p + (eps * vp if np_ else 0))
+        fm = O.rhs(system, t, y - eps * vy, p - (eps * vp if np_ else 0))
+        fd = (fp - fm) / (2 * eps)
+        assert np.allclose(j, fd, rtol=1e-6, atol=1e-8 * np.abs(fd).max()), system
+
+
+# ---------------------------------------------------------------------------------------------
+def test_converged_reference_self_check():
+    """Appendix A / D: a second reference solve 10x looser must agree within eps_req/10."""
+    e = W.mw(n=16, seed=16, t1=1000.0)
+    a = O.solve("mw", e.y0, e.params, e.t0, e.t1, e.saveat, 1e-13, 1e-13, method="vern7")["y"][:, -1]
+    b = O.solve("mw", e.y0, e.params, e.t0, e.t1, e.saveat, 1e-12, 1e-12, method="vern7")["y"][:, -1]
+    rE, vE = M.orbit_scales("mw", e.y0, e.params)
+    assert np.max(M.orbit_error(b, a, rE, vE)) < 1e-4 / 10
+
+
+# ---------------------------------------------------------------------------------------------
+def test_status_codes_and_nan_outputs():
+    e = W.isochrone(n=6, seed=17)
+    y0 = e.y0.copy()
+    y0[1, 2] = np.nan
+    t1 = e.t1.copy()
+    t1[2] = 0.0  # empty interval
+    sv = np.stack([e.saveat] * 6)
+    sv[3, 10] = 150.0  # outside [t0, t1]
+    sv[4, 6] = 45.0  # not non-decreasing: that point alone is rejected
+    res = O.solve("isochrone", y0, None, e.t0, t1, sv, 1e-8, 1e-8)
+    st = res["status"]
+    assert st[0] == 0
+    assert st[1] == O.ST_NONFINITE and np.all(np.isnan(res["y"][1]))
+    assert st[2] == O.ST_EMPTY_INTERVAL and np.array_equal(res["y"][2], np.repeat(y0[2:3], 11, 0))
+    assert st[3] & O.ST_SAVEAT_OUTSIDE
+    assert np.all(np.isnan(res["y"][3, 10])) and np.all(np.isfinite(res["y"][3, :10]))
+    assert st[4] == O.ST_SAVEAT_OUTSIDE and np.all(np.isnan(res["y"][4, 6]))
+    assert np.all(np.isfinite(np.delete(res["y"][4], 6, axis=0)))
+    res = O.solve("isochrone", e.y0, None, e.t0, e.t1, e.saveat, 1e-8, 1e-8, max_steps=20)
+    assert np.all(res["status"] == O.ST_MAX_STEPS) and np.all(np.isnan(res["y"]))
+    assert np.all(res["n_accept"] + res["n_reject"] == 20)
+    # outputs at t0 are the initial state exactly
+    res = O.solve("isochrone", e.y0, None, e.t0, e.t1, e.saveat, 1e-8, 1e-8)
+    assert np.array_equal(res["y"][:, 0], e.y0)
