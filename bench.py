@@ -1,0 +1,397 @@
+"""Benchmark: ensemble solves/s and forward+gradient solves/s at a fixed error budget, against the
+plain one-thread-per-trajectory FP64 kernel on the same GPU.
+
+Workload: 1,048,576 test-particle orbits in the Milky-Way-like potential (Miyamoto-Nagai disc +
+Hernquist bulge + z-flattened NFW halo, q ~ U[0.8, 1.2]), seeded ICs with R ~ U[4, 20] kpc,
+|z| < 2 kpc, near-circular velocities plus 20 km/s dispersion, integrated 0-3 Gyr with Tsit5;
+gradient of L = 1/2 sum ||y(t1) - y_tgt||^2 with respect to y0 and the 4 potential parameters.
+
+One step = one pass of the whole hot path over the ensemble: the adaptive forward solve recording
+its step tape, the loss cotangent, and the discrete-adjoint reverse sweep. Each variant runs at the
+loosest tolerance of the quarter-decade grid meeting the orbit budget P99(eps) <= 1e-4
+(Eq. accept, Eq. st-fwderr); the achieved error is measured on every run against a converged FP64
+Verner 7 solve (rtol 1e-12) of a sample of the same orbits.
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ensemble solves/s and fwd+grad solves/s at fixed error budget vs plain FP64 on GB300"
+N_ORBITS = 1 << 20
+T1_MYR = 3000.0
+BUDGET = 1e-4
+# loosest quarter-decade tolerances meeting the orbit budget on this workload (tolerance search of
+# the paper's Appendix A on a 4096-orbit draw; re-checked on every run below)
+RTOL_FP32 = 3.16e-8
+RTOL_FP64 = 5.62e-8
+RTOL_CONFIG = 3e-7  # the tolerance the workload is quoted at; it misses the budget here
+
+# Algorithmic flops (sqrt, div, log counted as one op each), Tsit5 on the MW system:
+#   f:   ~70 add/mul + 4 sqrt + 1 log + 3 div = 78;  VJP of f: ~2.5 f = 195
+#   forward attempt: 6 f (FSAL) + 2d (nnz A + nnz(b - bhat)) = 2*6*(21+7) + ~40 controller = 880
+#   reverse accepted step: 7 f (stage recompute incl. k1) + 2d nnz A (recompute) + 6 VJP
+#                          + 2d (nnz A + nnz b) (adjoint stage algebra) = 2292
+F_RHS_MW = 78
+F_ATT_FWD = 6 * F_RHS_MW + 2 * 6 * (21 + 7) + 40
+F_STEP_REV = 7 * F_RHS_MW + 2 * 6 * 21 + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (21 + 6)
+# FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 1.25  # nominal GB300 FP64 rate
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.strip()]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------------
+def cpu_oracle_rate(e, rtol, target_s=12.0, nmax=200000):
+    """The CPU oracle (FP64 same-algorithm solve + forward-sensitivity gradient) on a bounded sample
+    of the workload, all host cores. Returns (solves/s, cores, sample description)."""
+    import oracle as O
+
+    cores = O.max_threads()
+    rng = np.random.default_rng(7)
+    n = 256
+    while True:
+        idx = np.sort(rng.choice(e.n, n, replace=False))
+        s = e.subset(idx)
+        w = (rng.normal(size=(n, 1, 6)))
+        t = time.perf_counter()
+        O.grad("mw", s.y0, s.params, s.t0, s.t1, s.saveat, w, rtol=rtol, atol=rtol)
+        dt = time.perf_counter() - t
+        if dt * 4 > target_s or n * 4 > nmax:
+            return n / dt, cores, "%d of %d orbits (fwd + forward-sensitivity gradient), %.1f s" % (n, e.n, dt)
+        n *= 4
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2609_28458_gb300 import workloads as W
+
+    e = W.mw(n=N_ORBITS, seed=1000, t1=T1_MYR, rtol=RTOL_FP64)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(e, RTOL_FP64, target_s=1.0, nmax=1024)
+    t = time.perf_counter()
+    rates = []
+    for _ in range(args.steps):
+        r, cores, sample = cpu_oracle_rate(e, RTOL_FP64, target_s=8.0)
+        rates.append(r)
+    dt = time.perf_counter() - t
+    value = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "mw_1048576_orbits_0_3gyr", "system": "mw", "method": "tsit5", "rtol": RTOL_FP64,
+                       "note": "CPU oracle, fwd + gradient by forward sensitivities, bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    from paper_2609_28458_gb300 import api
+    from paper_2609_28458_gb300 import build as gsbuild
+    from paper_2609_28458_gb300 import metrics as M
+    from paper_2609_28458_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        gsbuild.build()
+    if world > 1:
+        dist.barrier()
+    gsbuild.build()
+
+    # each rank integrates its own shard of the ensemble (weak scaling: N orbits per GPU)
+    e = W.mw(n=args.n, seed=1000 + rank, t1=T1_MYR, rtol=RTOL_FP32)
+    N = e.n
+    y0 = torch.as_tensor(e.y0, device=dev)
+    pr = torch.as_tensor(e.params, device=dev)
+    t0 = torch.as_tensor(e.t0, device=dev)
+    t1 = torch.as_tensor(e.t1, device=dev)
+    sv = torch.as_tensor(e.saveat, device=dev)
+    # target: the endpoint of the same orbits with potential parameters perturbed by 1% (seeded)
+    rng = np.random.default_rng(77 + rank)
+    ptgt = torch.as_tensor(e.params * (1 + 0.01 * rng.standard_normal(e.params.shape)), device=dev)
+    y_tgt = api.solve("mw", y0, ptgt, t0, t1, sv, 1e-9, 1e-9, precision="fp64")["y"].clone()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def variant(prec, rtol, kernel="persistent"):
+        ws = api.Workspace(dev)
+        probe = api.solve("mw", y0, pr, t0, t1, sv, rtol, rtol, precision=prec, kernel=kernel)
+        tape_nbytes = api.tape_bytes("mw", N, n_accept=probe["n_accept"])
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+        def step():
+            s = api.solve("mw", y0, pr, t0, t1, sv, rtol, rtol, precision=prec, kernel=kernel, record_tape=True,
+                          workspace=ws, tape_nbytes=tape_nbytes)
+            ev[1].record(stream)
+            w = s["y"] - y_tgt  # dL/dy of L = 1/2 ||y(t1) - y_tgt||^2
+            ev[2].record(stream)
+            g = api.vjp("mw", y0, pr, t0, t1, sv, rtol, rtol, w, precision=prec, kernel=kernel, reuse_tape=s,
+                        workspace=ws)
+            return s, g
+
+        def fwd():
+            return api.solve("mw", y0, pr, t0, t1, sv, rtol, rtol, precision=prec, kernel=kernel)
+
+        return step, fwd, ev, ws
+
+    # ---------------- headline: FP32 stages, persistent kernels, tape reuse ----------------
+    step, fwd, ev, ws = variant("fp32", RTOL_FP32)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_fwd, t_rev = [], []
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev[0].record(stream)
+            s, g = step()
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            t_fwd.append(ev[0].elapsed_time(ev[1]))
+            t_rev.append(ev[2].elapsed_time(ev[3]))
+        stop.record(stream)
+        torch.cuda.synchronize()
+    total_ms = start.elapsed_time(stop)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = tt.item()
+    ms_per_step = total_ms / args.steps
+    value = world * N * args.steps / (total_ms / 1e3)
+    n_att = int((s["n_accept"].long() + s["n_reject"].long()).sum().item())
+    n_acc = int(s["n_accept"].long().sum().item())
+    n_bad = int((s["status"] != 0).sum().item())
+
+    # forward-only throughput of the same variant
+    for _ in range(2):
+        fwd()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a.record(stream)
+        fwd()
+        b.record(stream)
+        torch.cuda.synchronize()
+        fms.append(a.elapsed_time(b))
+    fwd_ms = float(np.mean(fms))
+
+    # accuracy against a converged FP64 Verner 7 solve (rtol 1e-12) of a sample of the same orbits
+    ns = min(N, args.acc_sample)
+    idx = torch.as_tensor(np.sort(np.random.default_rng(5).choice(N, ns, replace=False)), device=dev)
+    ref = api.solve("mw", y0[idx], pr[idx], t0[idx], t1[idx], sv, 1e-12, 1e-12, method="vern7", precision="fp64")
+    wref = (ref["y"] - y_tgt[idx])
+    gref = api.vjp("mw", y0[idx], pr[idx], t0[idx], t1[idx], sv, 1e-12, 1e-12, wref, method="vern7",
+                   precision="fp64", n_accept_hint=ref["n_accept"])
+    rE, vE = M.orbit_scales("mw", e.y0[idx.cpu().numpy()], e.params[idx.cpu().numpy()])
+    err = M.orbit_error(s["y"][idx, -1].cpu().numpy(), ref["y"][:, -1].cpu().numpy(), rE, vE)
+    gv = torch.cat([g["dLdy0"][idx], g["dLdparams"][idx]], 1).cpu().numpy()
+    gr = torch.cat([gref["dLdy0"], gref["dLdparams"]], 1).cpu().numpy()
+    gerr = np.linalg.norm(gv - gr, axis=1) / np.linalg.norm(gr, axis=1)
+
+    # roofline of the dominant kernel (FP32 ALU bound)
+    fwd_kernel_ms = float(np.mean(t_fwd))
+    rev_kernel_ms = float(np.mean(t_rev))
+    if rev_kernel_ms >= fwd_kernel_ms:
+        dom, flops, dur = "reverse (discrete adjoint, persistent, fp32 stages)", n_acc * F_STEP_REV, rev_kernel_ms
+    else:
+        dom, flops, dur = "forward (persistent, fp32 stages, tape record)", n_att * F_ATT_FWD, fwd_kernel_ms
+    achieved = flops / (dur / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+
+    # ---------------- end to end through the public API with host buffers ----------------
+    host = {k: torch.as_tensor(v).pin_memory() for k, v in
+            dict(y0=e.y0, p=e.params, t0=e.t0, t1=e.t1, sv=e.saveat, tgt=y_tgt.cpu().numpy()).items()}
+    out_y0 = torch.empty((N, 6), dtype=torch.float64).pin_memory()
+    out_p = torch.empty((N, 4), dtype=torch.float64).pin_memory()
+    dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
+    ws_e2e = api.Workspace(dev)
+    tape_nb = api.tape_bytes("mw", N, n_accept=s["n_accept"])
+
+    def e2e_step():
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        ss = api.solve("mw", dbuf["y0"], dbuf["p"], dbuf["t0"], dbuf["t1"], dbuf["sv"], RTOL_FP32, RTOL_FP32,
+                       precision="fp32", record_tape=True, workspace=ws_e2e, tape_nbytes=tape_nb)
+        gg = api.vjp("mw", dbuf["y0"], dbuf["p"], dbuf["t0"], dbuf["t1"], dbuf["sv"], RTOL_FP32, RTOL_FP32,
+                     ss["y"] - dbuf["tgt"], precision="fp32", reuse_tape=ss, workspace=ws_e2e)
+        out_y0.copy_(gg["dLdy0"], non_blocking=True)
+        out_p.copy_(gg["dLdparams"], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    ee = []
+    for _ in range(args.steps):
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ee.append(a.elapsed_time(b))
+    e2e_ms = float(np.mean(ee))
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = out_y0.numel() * 8 + out_p.numel() * 8
+
+    # ---------------- the plain one-thread-per-trajectory FP64 kernel ----------------
+    plain = {}
+    if not args.skip_plain:
+        stp, fw, evp, wsp = variant("fp64", RTOL_FP64, kernel="plain")
+        stp()
+        torch.cuda.synchronize()
+        a.record(stream); stp(); b.record(stream); torch.cuda.synchronize()
+        pg = a.elapsed_time(b)
+        a.record(stream); fw(); b.record(stream); torch.cuda.synchronize()
+        pf = a.elapsed_time(b)
+        plain = {"rtol": RTOL_FP64, "fwd_solves_per_s": N / (pf / 1e3), "fwd_grad_solves_per_s": N / (pg / 1e3),
+                 "fwd_ms": pf, "fwd_grad_ms": pg, "fwd_fp64_peak_frac_est": None}
+        del wsp
+
+    # the workload's quoted tolerance, for context (misses the budget on this workload)
+    stc, fwc, evc, wsc = variant("fp32", RTOL_CONFIG)
+    stc()
+    torch.cuda.synchronize()
+    a.record(stream); sc, gc = stc(); b.record(stream); torch.cuda.synchronize()
+    cfg_ms = a.elapsed_time(b)
+    err_cfg = M.orbit_error(sc["y"][idx, -1].cpu().numpy(), ref["y"][:, -1].cpu().numpy(), rE, vE)
+    del wsc
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        r, cores, sample = cpu_oracle_rate(e, RTOL_FP32)
+        cpu = {"value": r, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 stages / f64 norm, time, controller", "data": "synthetic",
+            "config": {"workload": "mw_1048576_orbits_0_3gyr", "N_per_gpu": N, "system": "mw", "method": "tsit5",
+                       "precision": "fp32_stages", "kernel": "persistent forward + persistent reverse, tape reuse",
+                       "rtol": RTOL_FP32, "atol": RTOL_FP32, "t1_myr": T1_MYR, "error_budget": BUDGET,
+                       "parallelism": "replicas (independent shards)" if world > 1 else "single GPU",
+                       "l2": "L2 flushed (256 MB write) before every timed step; tape ~%.0f GB" % (ws.nbytes / 1e9)},
+            "fwd_solves_per_s": world * N / (fwd_ms / 1e3), "fwd_ms": fwd_ms,
+            "kernel_ms": {"forward_record": fwd_kernel_ms, "reverse": rev_kernel_ms},
+            "accuracy": {"sample": ns, "p99_orbit_err": M.p99(err), "max_orbit_err": float(err.max()),
+                         "accepted": M.accepted(err, BUDGET), "grad_p99_rel_err": float(np.percentile(gerr, 99)),
+                         "grad_max_rel_err": float(gerr.max()), "failed_trajectories": n_bad,
+                         "reference": "FP64 Verner 7 rtol 1e-12 on the GPU (checked against the CPU oracle by tests)"},
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64": ({"fwd": plain["fwd_ms"] / fwd_ms, "fwd_grad": plain["fwd_grad_ms"] / ms_per_step}
+                                      if plain else None),
+            "at_quoted_rtol": {"rtol": RTOL_CONFIG, "fwd_grad_solves_per_s": N / (cfg_ms / 1e3),
+                               "p99_orbit_err": M.p99(err_cfg), "accepted": M.accepted(err_cfg, BUDGET)},
+            "step_attempts": {"mean": n_att / N, "accepted_mean": n_acc / N},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_ORBITS)
+    ap.add_argument("--acc-sample", type=int, default=16384)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/* gs.h — C ABI of the GB300 ensemble Runge-Kutta library (libgs.so).
+ *
+ * The library integrates n independent initial-value problems dy_i/dt = f(t, y_i, theta_i),
+ * y_i(t0_i) = y0_i (the ensemble problem, Sec. 2.1, Eq. ivp) with adaptive explicit Runge-Kutta
+ * pairs (Sec. 2.2; Appendix A, Eqs. rk, errnorm, controller, dense), one trajectory per GPU thread,
+ * and returns the gradient of a scalar loss through the solve by a discrete adjoint of the
+ * accepted step sequence (the reverse-mode counterpart of Appendix A, Eqs. adjoint, stage-sens).
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers to caller-owned memory, in row-major (C) order, FP64
+ *    unless stated. The library allocates no device memory; scratch space is the caller's
+ *    `workspace`. Nothing is freed by the library.
+ *  - Calls are asynchronous and ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ *    stream). Per-trajectory failures are reported in the `status` array, never by a trap.
+ *  - Return value: GS_OK (0) or a GS_ERR_* code; on a non-zero return nothing was launched and no
+ *    output was written. gs_last_error() then gives a message (thread-local).
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Systems (right-hand sides f):
+ *  GS_SYS_ISOCHRONE    d=6, p=0: test particle in Phi = -1/(1+sqrt(1+r^2)), G = M = b = 1.
+ *  GS_SYS_MW           d=6, p=4: Miyamoto-Nagai disc + Hernquist bulge + z-flattened NFW halo;
+ *                      theta = (M_disc, M_bulge, M_halo [1e10 Msun], q_halo); kpc, Myr units.
+ *  GS_SYS_PRECESSION   d=9, p=3: orbit-averaged spin precession in v (Sec. 5, Eqs. prec-spins,
+ *                      prec-L, prec-omega, prec-rr with 2PN b_k); theta = (q, chi1, chi2).
+ *  GS_SYS_QUINTESSENCE d=3, p=4: thawing quintessence in N = ln a (Sec. 4.1, Eq. de-model;
+ *                      Appendix C, Eq. de-rhs); y = (phi, u, I), theta = (a0, lambda, Om, Or).
+ *  GS_SYS_LOGHALO      d=6, p=3: flattened logarithmic halo (Sec. 3, Eq. loghalo);
+ *                      theta = (v_c, R_c, q).
+ */
+typedef enum {
+  GS_SYS_ISOCHRONE = 0,
+  GS_SYS_MW = 1,
+  GS_SYS_PRECESSION = 2,
+  GS_SYS_QUINTESSENCE = 3,
+  GS_SYS_LOGHALO = 4
+} gs_system;
+
+/* Runge-Kutta pairs (Sec. 2.2): Tsit5 and Dopri5 (order 5, FSAL, dense-output polynomial),
+ * Verner's 7(6) pair (order 7; outputs inside a step by a shortened step, Appendix A). */
+typedef enum { GS_TSIT5 = 0, GS_DOPRI5 = 1, GS_VERN7 = 2 } gs_method;
+
+/* GS_FP64: every operation in FP64.
+ * GS_FP32_STAGES: stage and right-hand-side arithmetic in FP32, the state kept as a compensated
+ *   FP32 pair, the error-norm accumulation, the time (compensated summation) and the step-size
+ *   controller in FP64. */
+typedef enum { GS_FP64 = 0, GS_FP32_STAGES = 1 } gs_precision;
+
+/* GS_KERNEL_PLAIN: one thread per trajectory for its whole solve (a warp waits for its slowest
+ *   member, Appendix A, Eq. cost). GS_KERNEL_PERSISTENT: persistent CTAs whose lanes take the next
+ *   trajectory from a device work queue as soon as their own one finishes. */
+typedef enum { GS_KERNEL_AUTO = 0, GS_KERNEL_PLAIN = 1, GS_KERNEL_PERSISTENT = 2 } gs_kernel;
+
+/* Per-trajectory status bits (status[n]). */
+#define GS_ST_OK 0
+#define GS_ST_MAX_STEPS 1       /* more than max_steps attempts; outputs NaN            */
+#define GS_ST_H_UNDERFLOW 2     /* h < 16 eps max(|t|,|t1|); outputs NaN                */
+#define GS_ST_NONFINITE 4       /* non-finite y0, theta, t0 or t1; outputs NaN          */
+#define GS_ST_EMPTY_INTERVAL 8  /* t1 <= t0: every output is y0, no step taken          */
+#define GS_ST_SAVEAT_OUTSIDE 16 /* an output time outside [t0,t1] or decreasing: NaN there */
+#define GS_ST_TAPE_OVERFLOW 32  /* gs_vjp: the step tape did not fit; gradients NaN     */
+
+/* Return codes. */
+#define GS_OK 0
+#define GS_ERR_INVALID 1   /* bad argument (null pointer, size, enum)        */
+#define GS_ERR_CUDA 2      /* a CUDA runtime call failed                     */
+#define GS_ERR_WORKSPACE 3 /* workspace missing or too small                 */
+
+typedef struct {
+  int32_t method;       /* gs_method                                                  */
+  int32_t precision;    /* gs_precision                                               */
+  int32_t kernel;       /* gs_kernel                                                  */
+  int32_t max_steps;    /* attempts per trajectory before GS_ST_MAX_STEPS (1e6)       */
+  double safety;        /* controller safety factor (0.9)                             */
+  double alpha_min;     /* smallest step ratio (0.2)                                  */
+  double alpha_max;     /* largest step ratio (5)                                     */
+  double beta1, beta2;  /* PI gains: h*clamp(safety*err^-beta1*err_prev^beta2);
+                           beta1 = 0 selects 1/nu and beta2 = 0 gives Eq. controller  */
+  double h0;            /* initial step; 0 = Hairer-Norsett-Wanner starting step      */
+  int32_t per_traj_saveat; /* saveat is [N,K] instead of [K]                          */
+  int32_t block_size;      /* threads per block; 0 = library default                  */
+  int32_t record_tape;     /* gs_solve: record the accepted steps into the workspace  */
+  int32_t reuse_tape;      /* gs_vjp: reverse the tape recorded by the preceding
+                              gs_solve (same inputs and options) instead of re-solving */
+  int32_t tape_capacity;   /* max accepted steps recorded per trajectory (65536)      */
+  int32_t reserved;
+} gs_options;
+
+/* Fill *opt with the defaults above (Tsit5, FP64, auto kernel). */
+void gs_default_options(gs_options* opt);
+
+/* State and parameter dimensions of a system. Returns GS_ERR_INVALID for an unknown id. */
+int gs_dims(int32_t system, int32_t* d, int32_t* p);
+
+/* Adaptive ensemble solve (Sec. 2.1-2.2; Appendix A, Eqs. rk, errnorm, controller, dense).
+ *  y0 [N,d], params [N,p] (may be NULL when p = 0), t0 [N], t1 [N]: inputs.
+ *  saveat [K] non-decreasing output times shared by all trajectories, or [N,K] if
+ *    opt->per_traj_saveat. An output at t0 is y0 exactly; an output at t1 is the final state.
+ *  y_out [N,K,d]: the solution at the output times (dense output inside steps).
+ *  status [N], n_accept [N], n_reject [N] (int32): per-trajectory status bits and step-attempt
+ *    counts (rejected attempts included in N_i = n_accept + n_reject, Sec. 2.2).
+ *  workspace / workspace_bytes: needed for the persistent kernel (work-queue counter) and for
+ *    opt->record_tape; size from gs_workspace_bytes. May be NULL otherwise.
+ */
+int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+             const double* t1, double rtol, double atol, int32_t K, const double* saveat,
+             const gs_options* opt, double* y_out, int32_t* status, int32_t* n_accept,
+             int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* Gradient of a scalar loss L through the solve, by the discrete adjoint of the accepted step
+ * sequence (the steps are held fixed, so the result is the exact derivative of the numerical
+ * solution on that sequence, Sec. 2.3 and Appendix A, Eq. stage-sens).
+ *  Inputs as gs_solve, plus dLdy [N,K,d], the cotangent of y_out.
+ *  dLdy0 [N,d], dLdparams [N,p] (may be NULL when p = 0): per-trajectory gradients; for
+ *    parameters shared by all members the caller sums over n (Appendix A, Eq. chain).
+ *  status [N]: as gs_solve, plus GS_ST_TAPE_OVERFLOW. Failed trajectories get NaN gradients.
+ *  y_out [N,K,d]: the forward solution of the internal re-solve (may be NULL with reuse_tape).
+ *  With opt->reuse_tape, status, n_accept and n_reject are INPUTS: the arrays written by the
+ *  recording gs_solve (status gains GS_ST_TAPE_OVERFLOW there); the forward solve is not re-run.
+ *  The workspace holds the step tape: per accepted step the state at its start, its time and
+ *  its length, in chunks taken from a pool by an atomic counter.
+ */
+int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+           const double* t1, double rtol, double atol, int32_t K, const double* saveat,
+           const gs_options* opt, const double* dLdy, double* dLdy0, double* dLdparams,
+           double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* workspace,
+           size_t workspace_bytes, void* cuda_stream);
+
+/* Workspace bytes for N trajectories. for_vjp = 0: the persistent kernel's counter only.
+ * for_vjp != 0: room for a step tape of `steps_hint` accepted steps per trajectory on average
+ * (rounded up to whole chunks per trajectory), plus the chunk table sized by
+ * opt->tape_capacity. A smaller workspace is accepted; trajectories whose steps no longer fit
+ * get GS_ST_TAPE_OVERFLOW. */
+size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
+                          double steps_hint);
+
+/* Evaluate f (Eq. ivp) and its vector-Jacobian products for M states, as the solver does:
+ *  f [M,d] = f(t, y, theta);  gy [M,d] = J_y^T w;  gp [M,p] = J_theta^T w  (gy, gp may be NULL).
+ *  precision selects the FP64 or FP32 instantiation. */
+int gs_rhs(int32_t system, int32_t precision, int64_t M, const double* t, const double* y,
+           const double* params, const double* w, double* f, double* gy, double* gp, void* cuda_stream);
+
+/* Message for the last non-zero return on this host thread ("" if none). */
+const char* gs_last_error(void);
+
+/* Library version string. */
+const char* gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

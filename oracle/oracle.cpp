@@ -210,7 +210,11 @@ void integrate(int sys, const Opts& o, const T* y0, const T* p, double t0, doubl
         last = true;
       } else {
         double tm = std::fabs(t) > std::fabs(t1) ? std::fabs(t) : std::fabs(t1);
-        if (h < 16.0 * DBL_EPSILON * tm) { *status |= ST_H_UNDERFLOW; failed = true; break; }
+        if (!(h >= 16.0 * DBL_EPSILON * tm)) {  // also catches a non-finite step size
+          *status |= std::isnan(h) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW;
+          failed = true;
+          break;
+        }
       }
     }
     stages(sys, tab, s, t, y, p, h, d, k);

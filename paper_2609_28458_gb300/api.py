@@ -1,0 +1,211 @@
+"""PyTorch-facing calls of the ensemble solver. Argument marshalling only: tensors are checked,
+made contiguous FP64 on the GPU, and their device pointers are handed to libgs.so together with
+the current CUDA stream. Torch provides device memory and streams; every step of the solve and of
+its gradient runs in the library's kernels.
+"""
+import ctypes
+
+import torch
+
+from . import _abi
+
+_i32 = torch.int32
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev(x, device, name):
+    """FP64 contiguous copy of x on `device`. The first tensor of a call (device None) must already
+    live on a CUDA device: it decides where the solve runs. Later arguments are moved there."""
+    if not torch.is_tensor(x):
+        x = torch.as_tensor(x, dtype=torch.float64)
+    if device is None:
+        if x.device.type != "cuda":
+            raise ValueError("%s must be a CUDA tensor (the solver runs only on the GPU)" % name)
+        device = x.device
+    return x.to(device=device, dtype=torch.float64).contiguous()
+
+
+def _vec(x, n, dev, name):
+    """A per-trajectory FP64 vector of length n on dev from a scalar, a NumPy array or a tensor."""
+    if not torch.is_tensor(x):
+        x = torch.as_tensor(x, dtype=torch.float64)
+    if x.dim() == 0 or x.numel() == 1:
+        return torch.full((n,), float(x.reshape(-1)[0]), dtype=torch.float64, device=dev)
+    return _dev(x, dev, name).reshape(n)
+
+
+def _sysid(system):
+    return _abi.SYSTEMS[system] if isinstance(system, str) else int(system)
+
+
+class Workspace:
+    """A reusable device workspace (256-byte aligned torch allocation)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device(device or "cuda")
+        self.buf = None
+
+    def get(self, nbytes):
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    @property
+    def nbytes(self):
+        return 0 if self.buf is None else self.buf.numel()
+
+
+_default_ws = {}
+
+
+def _ws(device, nbytes, ws):
+    """Exactly `nbytes` of a (possibly larger, reused) workspace buffer."""
+    if ws is None:
+        ws = _default_ws.setdefault(str(device), Workspace(device))
+    return ws.get(nbytes)[: int(nbytes)]
+
+
+def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None):
+    """Workspace bytes for a tape: exact from per-trajectory accepted-step counts, else from a hint."""
+    d, _ = _abi.dims(system)
+    opt = opt or _abi.options()
+    fixed = _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 0, 0.0)
+    chunk = 16 + 32 * (8 * d + 32)
+    if n_accept is not None:
+        chunks = int(((n_accept.to(torch.int64) + 31) // 32).sum().item()) + 1
+        return fixed + chunks * chunk
+    return _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 1, float(steps_hint or 1024))
+
+
+def solve(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precision="fp64", kernel="auto",
+          workspace=None, record_tape=False, tape_nbytes=None, out=None, **kw):
+    """Adaptive ensemble solve. Returns dict(y [N,K,d], status, n_accept, n_reject) on the GPU."""
+    y0 = _dev(y0, None, "y0")
+    dev = y0.device
+    d, p = _abi.dims(system)
+    N = y0.shape[0]
+    y0 = y0.reshape(N, d)
+    params = _dev(params, dev, "params").reshape(N, p) if p else None
+    t0 = _vec(t0, N, dev, "t0")
+    t1 = _vec(t1, N, dev, "t1")
+    saveat = _dev(saveat, dev, "saveat")
+    per_traj = saveat.dim() == 2
+    K = saveat.shape[-1]
+    steps_hint = kw.pop("steps_hint", 1024)
+    opt = _abi.options(method, precision, kernel, per_traj_saveat=int(per_traj), record_tape=int(record_tape), **kw)
+    if out is None:
+        out = dict(y=torch.empty((N, K, d), dtype=torch.float64, device=dev),
+                   status=torch.empty(N, dtype=_i32, device=dev), n_accept=torch.empty(N, dtype=_i32, device=dev),
+                   n_reject=torch.empty(N, dtype=_i32, device=dev))
+    if record_tape:
+        nbytes = tape_nbytes or tape_bytes(system, N, steps_hint=steps_hint, opt=opt)
+    else:
+        nbytes = _abi.lib().gs_workspace_bytes(_sysid(system), N, K, ctypes.byref(opt), 0, 0.0)
+    wsb = _ws(dev, nbytes, workspace)
+    _abi.check(_abi.lib().gs_solve(_sysid(system), N, _ptr(y0), _ptr(params), _ptr(t0), _ptr(t1), float(rtol),
+                                   float(atol), K, _ptr(saveat), ctypes.byref(opt), _ptr(out["y"]),
+                                   _ptr(out["status"]), _ptr(out["n_accept"]), _ptr(out["n_reject"]), _ptr(wsb),
+                                   wsb.numel(), _stream(dev)))
+    return out
+
+
+def vjp(system, y0, params, t0, t1, saveat, rtol, atol, dLdy, method="tsit5", precision="fp64", kernel="auto",
+        workspace=None, reuse_tape=None, n_accept_hint=None, tape_nbytes=None, **kw):
+    """Discrete-adjoint gradient. Returns dict(dLdy0 [N,d], dLdparams [N,p], y, status, n_accept, n_reject).
+
+    reuse_tape: the result dict of a ``solve(..., record_tape=True, workspace=workspace)`` with the
+    same inputs; its tape (in `workspace`) is reversed instead of re-running the forward solve."""
+    y0 = _dev(y0, None, "y0")
+    dev = y0.device
+    d, p = _abi.dims(system)
+    N = y0.shape[0]
+    y0 = y0.reshape(N, d)
+    params = _dev(params, dev, "params").reshape(N, p) if p else None
+    t0 = _vec(t0, N, dev, "t0")
+    t1 = _vec(t1, N, dev, "t1")
+    saveat = _dev(saveat, dev, "saveat")
+    per_traj = saveat.dim() == 2
+    K = saveat.shape[-1]
+    dLdy = _dev(dLdy, dev, "dLdy").reshape(N, K, d)
+    steps_hint = kw.pop("steps_hint", 1024)
+    opt = _abi.options(method, precision, kernel, per_traj_saveat=int(per_traj), reuse_tape=int(reuse_tape is not None),
+                       **kw)
+    if reuse_tape:
+        if workspace is None:
+            raise ValueError("reuse_tape needs the workspace the tape was recorded into")
+        wsb = workspace.buf
+    else:
+        nbytes = tape_nbytes or tape_bytes(system, N, n_accept=n_accept_hint, steps_hint=steps_hint, opt=opt)
+        wsb = _ws(dev, nbytes, workspace)
+    res = dict(dLdy0=torch.empty((N, d), dtype=torch.float64, device=dev),
+               dLdparams=torch.empty((N, max(p, 0)), dtype=torch.float64, device=dev))
+    if reuse_tape is not None:
+        res.update(y=reuse_tape["y"], status=reuse_tape["status"], n_accept=reuse_tape["n_accept"],
+                   n_reject=reuse_tape["n_reject"])
+    else:
+        res.update(y=torch.empty((N, K, d), dtype=torch.float64, device=dev),
+                   status=torch.empty(N, dtype=_i32, device=dev), n_accept=torch.empty(N, dtype=_i32, device=dev),
+                   n_reject=torch.empty(N, dtype=_i32, device=dev))
+    _abi.check(_abi.lib().gs_vjp(_sysid(system), N, _ptr(y0), _ptr(params), _ptr(t0), _ptr(t1), float(rtol), float(atol),
+                                 K, _ptr(saveat), ctypes.byref(opt), _ptr(dLdy), _ptr(res["dLdy0"]),
+                                 _ptr(res["dLdparams"]), _ptr(res["y"]), _ptr(res["status"]), _ptr(res["n_accept"]),
+                                 _ptr(res["n_reject"]), _ptr(wsb), wsb.numel(), _stream(dev)))
+    return res
+
+
+def rhs(system, t, y, params=None, w=None, precision="fp64"):
+    """f(t, y, theta) and, if w is given, J_y^T w and J_theta^T w, evaluated by the device code."""
+    y = _dev(y, None, "y")
+    dev = y.device
+    d, p = _abi.dims(system)
+    M = y.shape[0]
+    t = _vec(t, M, dev, "t")
+    params = _dev(params, dev, "params").reshape(M, p) if p else None
+    f = torch.empty((M, d), dtype=torch.float64, device=dev)
+    gy = gp = None
+    if w is not None:
+        w = _dev(w, dev, "w").reshape(M, d)
+        gy = torch.empty((M, d), dtype=torch.float64, device=dev)
+        gp = torch.empty((M, max(p, 1)), dtype=torch.float64, device=dev) if p else None
+    _abi.check(_abi.lib().gs_rhs(_sysid(system), _abi.PRECISIONS[precision], M, _ptr(t), _ptr(y), _ptr(params),
+                                 _ptr(w) if w is not None else None, _ptr(f), _ptr(gy), _ptr(gp), _stream(dev)))
+    return f, gy, gp
+
+
+class GsSolve(torch.autograd.Function):
+    """y = solve(y0, params) with the discrete adjoint as backward (torch autograd wiring)."""
+
+    @staticmethod
+    def forward(ctx, y0, params, system, t0, t1, saveat, rtol, atol, opts):
+        r = solve(system, y0, params, t0, t1, saveat, rtol, atol, **opts)
+        ctx.save_for_backward(y0, params if params is not None else torch.empty(0, device=y0.device), t0, t1, saveat,
+                              r["n_accept"])
+        ctx.cfg = (system, rtol, atol, opts)
+        ctx.mark_non_differentiable(r["status"])
+        return r["y"], r["status"]
+
+    @staticmethod
+    def backward(ctx, gy, gstatus):
+        y0, params, t0, t1, saveat, n_acc = ctx.saved_tensors
+        system, rtol, atol, opts = ctx.cfg
+        _, p = _abi.dims(system)
+        o = {k: v for k, v in opts.items() if k not in ("record_tape",)}
+        r = vjp(system, y0, params if p else None, t0, t1, saveat, rtol, atol, gy.contiguous(), n_accept_hint=n_acc, **o)
+        return r["dLdy0"], (r["dLdparams"] if p else None), None, None, None, None, None, None, None
+
+
+def solve_autograd(system, y0, params, t0, t1, saveat, rtol, atol, **opts):
+    """Differentiable solve: returns (y [N,K,d], status); y.backward() runs gs_vjp."""
+    dev = y0.device
+    N = y0.shape[0]
+    t0 = torch.as_tensor(t0, dtype=torch.float64, device=dev).expand(N).contiguous()
+    t1 = torch.as_tensor(t1, dtype=torch.float64, device=dev).expand(N).contiguous()
+    saveat = torch.as_tensor(saveat, dtype=torch.float64, device=dev)
+    return GsSolve.apply(y0, params, system, t0, t1, saveat, rtol, atol, opts)

@@ -1,0 +1,265 @@
+// Discrete adjoint of the accepted step sequence (the reverse-mode counterpart of Appendix A,
+// Eqs. adjoint and stage-sens). The forward pass records, per accepted step, the state at its
+// start, t, tc, h and whether it was the last (clipped) step. The reverse pass walks that tape
+// backwards; for each step it recomputes the stages from the recorded state with h held fixed
+// (the same device code as the forward attempt) and propagates the cotangent through Eq. rk:
+//   y+ = y + h sum_j b_j k_j,   k_j = f(t + c_j h, Y_j),   Y_j = y + h sum_{l<j} a_jl k_l
+//   kbar_j = h (b_j ybar+ + sum_{l>j} a_lj Ybar_l) + dense-output injections,
+//   Ybar_j = J_y(Y_j)^T kbar_j,   thetabar += J_theta(Y_j)^T kbar_j,   ybar = ybar+ + sum_j Ybar_j.
+// Output cotangents dL/dy(t_k) enter at the step that produced y(t_k): through the dense-output
+// weights b_j(sigma) (Eq. dense) for Tsit5/Dopri5, through a shortened step for Verner 7, or
+// directly on y+ / y0 for outputs at t1 / t0. Since h is held fixed, the result is the exact
+// derivative of the numerical solution on the recorded steps (Sec. 2.3).
+#pragma once
+#include "gs_stepper.cuh"
+
+namespace gs {
+
+template <template <class> class SysT, class Tab, bool F32>
+struct Adjoint {
+  using T = Traj<SysT, Tab, F32>;
+  using R = typename T::R;
+  using Sys = typename T::Sys;
+  static constexpr int D = T::D, NP = T::NP, S = Tab::S, NPA = T::NPA;
+
+  struct PAcc {  // accumulator of theta-bar: FP64, or a compensated FP32 pair
+    R s[NPA], c[NPA];
+    __device__ void zero() {
+#pragma unroll
+      for (int q = 0; q < NPA; q++) { s[q] = R(0); c[q] = R(0); }
+    }
+    __device__ void add(int q, R v) {
+      if constexpr (F32) {
+        R ns, e;
+        two_sum(s[q], v, ns, e);
+        s[q] = ns;
+        c[q] += e;
+      } else {
+        s[q] += v;
+      }
+    }
+    __device__ double get(int q) const { return double(s[q]) + double(c[q]); }
+  };
+
+  // Reverse through stages 0..jmax-1 of a step of length hh whose stage states are Y and whose
+  // stage cotangents are kbar (consumed). Adds to ybar and pacc.
+  __device__ static void reverse_stages(const T& tr, double tt, double hh, R (*Y)[D], R (*kbar)[D], int jmax,
+                                        R* ybar, PAcc& pacc) {
+    const R hr = R(hh);
+#pragma unroll
+    for (int j = S - 1; j >= 0; j--) {
+      if (j < jmax) {
+        R gy[D], gp[NPA];
+        Sys::vjp(tr.stage_time(tt + Tab::c(j) * hh), Y[j], tr.p, kbar[j], gy, gp);
+#pragma unroll
+        for (int i = 0; i < D; i++) ybar[i] += gy[i];
+#pragma unroll
+        for (int q = 0; q < NP; q++) pacc.add(q, gp[q]);
+#pragma unroll
+        for (int l = 0; l < j; l++) {
+          if (Tab::a(j, l) != 0.0) {
+            const R c = hr * R(Tab::a(j, l));
+#pragma unroll
+            for (int i = 0; i < D; i++) kbar[l][i] += c * gy[i];
+          }
+        }
+      }
+    }
+  }
+
+  struct SlotView {
+    double t, tc, h;
+    bool last;
+  };
+
+  __device__ static const unsigned char* slot_ptr(const Problem& pb, int32_t chunk, int o) {
+    return pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader + (long long)o * T::kSlotBytes;
+  }
+  __device__ static int32_t prev_chunk(const Problem& pb, int32_t chunk) {
+    return int32_t(*reinterpret_cast<const long long*>(pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes));
+  }
+  __device__ static SlotView load_times(const unsigned char* s) {
+    const double* tail = reinterpret_cast<const double*>(s + 8 * D);
+    SlotView v;
+    v.t = tail[0]; v.tc = tail[1]; v.h = tail[2]; v.last = tail[3] != 0.0;
+    return v;
+  }
+  __device__ static void load_state(const unsigned char* s, T& tr) {
+    if constexpr (F32) {
+      const float* f = reinterpret_cast<const float*>(s);
+#pragma unroll
+      for (int i = 0; i < D; i++) { tr.y[i] = f[i]; tr.ylo[i] = f[D + i]; }
+    } else {
+      const double* f = reinterpret_cast<const double*>(s);
+#pragma unroll
+      for (int i = 0; i < D; i++) tr.y[i] = f[i];
+    }
+  }
+
+  __device__ static bool inside(const SlotView& v, double sv) {
+    return v.last || ((sv - v.t) + v.tc) <= v.h;
+  }
+
+  // ---- reverse sweep of one trajectory as a state machine: init(), step() per recorded step,
+  // finish(); the plain kernel runs it per thread, the persistent one refills lanes.
+  T tr;
+  R ybar[D];
+  PAcc pacc;
+  const double* W;
+  int kk, a;
+  int32_t chunk;
+  bool done;
+
+  __device__ void write_const(const Problem& pb, double v_y, double v_p, bool sum_w, bool only_t0) {
+    const long long n = tr.n;
+    double* gy0 = pb.dLdy0 + n * D;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      double acc = v_y;
+      if (sum_w) {
+        acc = 0.0;
+        for (int k = 0; k < pb.K; k++)
+          if (!only_t0 || (save_valid(pb, n, k, tr.t0, tr.t1) && save_at(pb, n, k) == tr.t0)) acc += W[k * D + i];
+      }
+      gy0[i] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < NP; q++) pb.dLdp[n * NP + q] = v_p;
+  }
+
+  __device__ void init(const Problem& pb, long long n) {
+    done = false;
+    tr.n = n;
+    tr.t0 = pb.t0[n];
+    tr.t1 = pb.t1[n];
+    W = pb.dLdy + n * (long long)pb.K * D;
+    const int32_t st = pb.status[n];
+    const int32_t nrec = pb.tape.n_rec[n];
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+    if ((st & ST_FAILED) || nrec < 0) { write_const(pb, nanv, nanv, false, false); done = true; return; }
+    if (st & ST_EMPTY) { write_const(pb, 0.0, 0.0, true, false); done = true; return; }  // outputs are y0
+    if (nrec == 0) { write_const(pb, 0.0, 0.0, true, true); done = true; return; }
+#pragma unroll
+    for (int q = 0; q < NP; q++) tr.p[q] = R(pb.params[n * NP + q]);
+    if (NP == 0) tr.p[0] = R(0);
+#pragma unroll
+    for (int i = 0; i < D; i++) ybar[i] = R(0);
+    pacc.zero();
+    kk = pb.K - 1;
+    a = nrec - 1;
+    chunk = pb.tape.head[n];
+    const SlotView last = load_times(slot_ptr(pb, chunk, a % kChunk));
+    // outputs emitted after the final step when the interval closed without a clipped last step
+    while (kk >= 0) {
+      if (!save_valid(pb, n, kk, tr.t0, tr.t1)) { kk--; continue; }
+      const double sv = save_at(pb, n, kk);
+      if (sv == tr.t0 || inside(last, sv)) break;
+#pragma unroll
+      for (int i = 0; i < D; i++) ybar[i] += R(W[kk * D + i]);
+      kk--;
+    }
+  }
+
+  // Reverse of recorded step a (ybar holds the cotangent of the state after it).
+  __device__ void step(const Problem& pb) {
+    const long long n = tr.n;
+    const double t0 = tr.t0, t1 = tr.t1;
+    const int o = a % kChunk;
+    const unsigned char* sp = slot_ptr(pb, chunk, o);
+    const int32_t pchunk = (o == 0 && a > 0) ? prev_chunk(pb, chunk) : chunk;
+    const SlotView cur = load_times(sp);
+    SlotView prev;
+    if (a > 0) prev = load_times(slot_ptr(pb, pchunk, o == 0 ? kChunk - 1 : o - 1));
+    load_state(sp, tr);
+    Sys::f(tr.stage_time(cur.t), tr.y, tr.p, tr.k1);
+    R k[S][D], Y[S][D], kbar[S][D];
+    tr.stages(cur.t, cur.h, k, Y, S);
+#pragma unroll
+    for (int j = 0; j < S; j++)
+#pragma unroll
+      for (int i = 0; i < D; i++) kbar[j][i] = R(0);
+    // cotangents reaching the step's start state directly (identity term of an output inside it)
+    R ydir[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) ydir[i] = R(0);
+    bool used_last_stage = false;
+    const R hr = R(cur.h);
+    // output cotangents of this step, latest first
+    while (kk >= 0) {
+      if (!save_valid(pb, n, kk, t0, t1)) { kk--; continue; }
+      const double sv = save_at(pb, n, kk);
+      if (sv == t0) break;
+      if (!inside(cur, sv)) break;
+      if (a > 0 && inside(prev, sv)) break;
+      R w[D];
+#pragma unroll
+      for (int i = 0; i < D; i++) w[i] = R(W[kk * D + i]);
+      if (cur.last && sv == t1) {
+#pragma unroll
+        for (int i = 0; i < D; i++) ybar[i] += w[i];  // y(t1) is the new state itself
+      } else {
+        double sig = ((sv - cur.t) + cur.tc) / cur.h;
+        if (sig > 1.0) sig = 1.0;
+        if (sig < 0.0) sig = 0.0;
+        if constexpr (Tab::DENSE_POLY) {
+          // y(t_k) = y + h sum_j b_j(sig) k_j
+          R wd[S];
+          Tab::dense(R(sig), wd);
+#pragma unroll
+          for (int j = 0; j < S; j++)
+#pragma unroll
+            for (int i = 0; i < D; i++) kbar[j][i] += hr * wd[j] * w[i];
+          used_last_stage = true;
+#pragma unroll
+          for (int i = 0; i < D; i++) ydir[i] += w[i];
+        } else {
+          // Verner 7: y(t_k) = shortened step of length sig*h from (t, y)
+          const double hs = sig * cur.h;
+          R ks[S][D], Ys[S][D], kbs[S][D];
+          tr.stages(cur.t, hs, ks, Ys, Tab::NREV);
+          const R hsr = R(hs);
+#pragma unroll
+          for (int j = 0; j < S; j++)
+#pragma unroll
+            for (int i = 0; i < D; i++) kbs[j][i] = (j < Tab::NREV) ? hsr * R(Tab::b(j)) * w[i] : R(0);
+#pragma unroll
+          for (int i = 0; i < D; i++) ydir[i] += w[i];
+          reverse_stages(tr, cur.t, hs, Ys, kbs, Tab::NREV, ydir, pacc);
+        }
+      }
+      kk--;
+    }
+    // the step itself: kbar_j += h b_j ybar, then the stages in reverse
+#pragma unroll
+    for (int j = 0; j < S; j++)
+      if (Tab::b(j) != 0.0)
+#pragma unroll
+        for (int i = 0; i < D; i++) kbar[j][i] += hr * R(Tab::b(j)) * ybar[i];
+#pragma unroll
+    for (int i = 0; i < D; i++) ybar[i] += ydir[i];
+    reverse_stages(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc);
+    chunk = pchunk;
+    a -= 1;
+    if (a < 0) finish(pb);
+  }
+
+  __device__ void finish(const Problem& pb) {
+    const long long n = tr.n;
+    // outputs at t0 are y0 itself
+    while (kk >= 0) {
+      if (save_valid(pb, n, kk, tr.t0, tr.t1) && save_at(pb, n, kk) == tr.t0) {
+#pragma unroll
+        for (int i = 0; i < D; i++) ybar[i] += R(W[kk * D + i]);
+      }
+      kk--;
+    }
+    double* gy0 = pb.dLdy0 + n * D;
+#pragma unroll
+    for (int i = 0; i < D; i++) gy0[i] = double(ybar[i]);
+#pragma unroll
+    for (int q = 0; q < NP; q++) pb.dLdp[n * NP + q] = pacc.get(q);
+    done = true;
+  }
+};
+
+}  // namespace gs

@@ -1,0 +1,293 @@
+// C ABI of libgs.so (declared in include/gs.h): argument checks, workspace layout and dispatch to
+// the per-system launchers. Nothing here allocates device memory; every call is stream-ordered.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gs.h"
+#include "gs_kernels.cuh"
+
+namespace gs {
+GS_DECLARE_SYSTEM(isochrone)
+GS_DECLARE_SYSTEM(mw)
+GS_DECLARE_SYSTEM(precession)
+GS_DECLARE_SYSTEM(quintessence)
+GS_DECLARE_SYSTEM(loghalo)
+}  // namespace gs
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int dims_of(int32_t sys, int32_t* d, int32_t* p) {
+  switch (sys) {
+    case GS_SYS_ISOCHRONE: *d = 6; *p = 0; return 0;
+    case GS_SYS_MW: *d = 6; *p = 4; return 0;
+    case GS_SYS_PRECESSION: *d = 9; *p = 3; return 0;
+    case GS_SYS_QUINTESSENCE: *d = 3; *p = 4; return 0;
+    case GS_SYS_LOGHALO: *d = 6; *p = 3; return 0;
+    default: return 1;
+  }
+}
+
+int order_of(int32_t method) { return method == GS_VERN7 ? 7 : 5; }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// bytes of one tape slot: state (8 d bytes in both precisions) + t, tc, h, flag
+long long slot_bytes(int32_t d) { return 8LL * d + 32; }
+long long chunk_bytes(int32_t d) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d); }
+
+// workspace: [0,256) header (queue counter at 0, pool counter at 8) | head[N] | n_rec[N] | pool
+struct Layout {
+  size_t header, head, nrec, pool, total_fixed;
+};
+Layout layout(int64_t N) {
+  Layout L;
+  L.header = 0;
+  L.head = 256;
+  L.nrec = L.head + align256(size_t(N) * 4);
+  L.pool = L.nrec + align256(size_t(N) * 4);
+  L.total_fixed = L.pool;
+  return L;
+}
+
+typedef cudaError_t (*fwd_fn)(const gs::Problem&, const gs::LaunchCfg&);
+fwd_fn forward_of(int32_t sys) {
+  switch (sys) {
+    case GS_SYS_ISOCHRONE: return gs::forward_isochrone;
+    case GS_SYS_MW: return gs::forward_mw;
+    case GS_SYS_PRECESSION: return gs::forward_precession;
+    case GS_SYS_QUINTESSENCE: return gs::forward_quintessence;
+    default: return gs::forward_loghalo;
+  }
+}
+fwd_fn reverse_of(int32_t sys) {
+  switch (sys) {
+    case GS_SYS_ISOCHRONE: return gs::reverse_isochrone;
+    case GS_SYS_MW: return gs::reverse_mw;
+    case GS_SYS_PRECESSION: return gs::reverse_precession;
+    case GS_SYS_QUINTESSENCE: return gs::reverse_quintessence;
+    default: return gs::reverse_loghalo;
+  }
+}
+
+int check_common(int32_t sys, int64_t N, const double* y0, const double* params, const double* t0,
+                 const double* t1, double rtol, double atol, int32_t K, const double* saveat,
+                 const gs_options* opt, int32_t* d, int32_t* p) {
+  if (dims_of(sys, d, p)) return fail(GS_ERR_INVALID, "unknown system id %d", sys);
+  if (!opt) return fail(GS_ERR_INVALID, "opt is NULL");
+  if (N < 0) return fail(GS_ERR_INVALID, "N < 0");
+  if (N > (int64_t(1) << 31) - 4096) return fail(GS_ERR_INVALID, "N too large (max 2^31 - 4096)");
+  if (K < 0) return fail(GS_ERR_INVALID, "K < 0");
+  if (opt->method < 0 || opt->method > 2) return fail(GS_ERR_INVALID, "unknown method %d", opt->method);
+  if (opt->precision < 0 || opt->precision > 1) return fail(GS_ERR_INVALID, "unknown precision %d", opt->precision);
+  if (opt->kernel < 0 || opt->kernel > 2) return fail(GS_ERR_INVALID, "unknown kernel %d", opt->kernel);
+  if (opt->block_size < 0 || opt->block_size > 128 || (opt->block_size % 32) != 0)
+    return fail(GS_ERR_INVALID, "block_size must be 0 or a multiple of 32 up to 128");
+  if (!(rtol >= 0.0) || !(atol >= 0.0) || !(rtol + atol > 0.0) || !std::isfinite(rtol) || !std::isfinite(atol))
+    return fail(GS_ERR_INVALID, "tolerances must be finite, non-negative and not both zero");
+  if (!(opt->safety > 0.0) || !(opt->alpha_min > 0.0) || !(opt->alpha_max >= opt->alpha_min))
+    return fail(GS_ERR_INVALID, "controller: need safety > 0 and 0 < alpha_min <= alpha_max");
+  if (opt->max_steps < 0) return fail(GS_ERR_INVALID, "max_steps < 0");
+  if (N > 0) {
+    if (!y0 || !t0 || !t1) return fail(GS_ERR_INVALID, "y0, t0 and t1 must not be NULL");
+    if (*p > 0 && !params) return fail(GS_ERR_INVALID, "params must not be NULL for this system");
+    if (K > 0 && !saveat) return fail(GS_ERR_INVALID, "saveat must not be NULL when K > 0");
+  }
+  return GS_OK;
+}
+
+gs::Problem make_problem(int64_t N, const double* y0, const double* params, const double* t0, const double* t1,
+                         double rtol, double atol, int32_t K, const double* saveat, const gs_options* opt) {
+  gs::Problem pb;
+  std::memset(&pb, 0, sizeof(pb));
+  pb.N = N;
+  pb.K = K;
+  pb.per_traj = opt->per_traj_saveat ? 1 : 0;
+  pb.y0 = y0; pb.params = params; pb.t0 = t0; pb.t1 = t1; pb.saveat = saveat;
+  pb.rtol = rtol; pb.atol = atol;
+  pb.max_steps = opt->max_steps;
+  pb.safety = opt->safety; pb.alpha_min = opt->alpha_min; pb.alpha_max = opt->alpha_max;
+  pb.beta1 = opt->beta1 > 0.0 ? opt->beta1 : 1.0 / order_of(opt->method);
+  pb.beta2 = opt->beta2;
+  pb.h0 = opt->h0;
+  return pb;
+}
+
+int set_tape(gs::Problem& pb, int32_t d, int64_t N, void* ws, size_t ws_bytes) {
+  Layout L = layout(N);
+  if (!ws) return fail(GS_ERR_WORKSPACE, "this call needs a workspace (see gs_workspace_bytes)");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(GS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < L.total_fixed + size_t(chunk_bytes(d)))
+    return fail(GS_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu needed for N = %lld", ws_bytes,
+                size_t(L.total_fixed + chunk_bytes(d)), (long long)N);
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  pb.tape.pool = base + L.pool;
+  pb.tape.chunk_bytes = chunk_bytes(d);
+  pb.tape.pool_chunks = (long long)((ws_bytes - L.pool) / size_t(chunk_bytes(d)));
+  if (pb.tape.pool_chunks > 0x7fffffffLL) pb.tape.pool_chunks = 0x7fffffffLL;
+  pb.tape.pool_next = reinterpret_cast<unsigned long long*>(base + 8);
+  pb.tape.head = reinterpret_cast<int32_t*>(base + L.head);
+  pb.tape.n_rec = reinterpret_cast<int32_t*>(base + L.nrec);
+  return GS_OK;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+void gs_default_options(gs_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->method = GS_TSIT5;
+  o->precision = GS_FP64;
+  o->kernel = GS_KERNEL_AUTO;
+  o->max_steps = 1000000;
+  o->safety = 0.9;
+  o->alpha_min = 0.2;
+  o->alpha_max = 5.0;
+  o->beta1 = 0.0;
+  o->beta2 = 0.0;
+  o->h0 = 0.0;
+  o->tape_capacity = 65536;
+}
+
+int gs_dims(int32_t system, int32_t* d, int32_t* p) {
+  if (!d || !p) return fail(GS_ERR_INVALID, "d and p must not be NULL");
+  if (dims_of(system, d, p)) return fail(GS_ERR_INVALID, "unknown system id %d", system);
+  return GS_OK;
+}
+
+size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
+                          double steps_hint) {
+  (void)K;
+  (void)opt;
+  int32_t d, p;
+  if (dims_of(system, &d, &p) || N < 0) return 0;
+  Layout L = layout(N);
+  if (!for_vjp) return L.total_fixed;
+  if (!(steps_hint > 0.0)) steps_hint = 1.0;
+  const double chunks = double(N) * (std::ceil(steps_hint / gs::kChunk) + 1.0) + 1.0;
+  return L.total_fixed + size_t(chunks) * size_t(chunk_bytes(d));
+}
+
+int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+             const double* t1, double rtol, double atol, int32_t K, const double* saveat,
+             const gs_options* opt, double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject,
+             void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  int32_t d, p;
+  int rc = check_common(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, &d, &p);
+  if (rc) return rc;
+  if (N > 0 && ((K > 0 && !y_out) || !status || !n_accept || !n_reject))
+    return fail(GS_ERR_INVALID, "outputs must not be NULL");
+  if (N == 0) return GS_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  gs::Problem pb = make_problem(N, y0, params, t0, t1, rtol, atol, K, saveat, opt);
+  pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
+  const int kernel = opt->kernel == GS_KERNEL_AUTO ? GS_KERNEL_PERSISTENT : opt->kernel;
+  const bool need_ws = kernel == GS_KERNEL_PERSISTENT || opt->record_tape;
+  if (need_ws) {
+    if (!workspace) return fail(GS_ERR_WORKSPACE, "the persistent kernel and tape recording need a workspace");
+    if (workspace_bytes < 256) return fail(GS_ERR_WORKSPACE, "workspace smaller than 256 bytes");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(GS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    pb.queue = static_cast<unsigned int*>(workspace);
+  }
+  if (opt->record_tape) {
+    rc = set_tape(pb, d, N, workspace, workspace_bytes);
+    if (rc) return rc;
+    pb.record = 1;
+  }
+  if (need_ws) {
+    cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  }
+  gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s};
+  cudaError_t e = forward_of(system)(pb, c);
+  if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  return GS_OK;
+}
+
+int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+           const double* t1, double rtol, double atol, int32_t K, const double* saveat, const gs_options* opt,
+           const double* dLdy, double* dLdy0, double* dLdparams, double* y_out, int32_t* status,
+           int32_t* n_accept, int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  int32_t d, p;
+  int rc = check_common(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, &d, &p);
+  if (rc) return rc;
+  if (N > 0 && ((K > 0 && !dLdy) || !dLdy0 || (p > 0 && !dLdparams) || !status || !n_accept || !n_reject))
+    return fail(GS_ERR_INVALID, "dLdy, dLdy0, dLdparams, status and step counts must not be NULL");
+  if (N == 0) return GS_OK;
+  if (!opt->reuse_tape && K > 0 && !y_out)
+    return fail(GS_ERR_INVALID, "y_out must not be NULL when the forward solve is re-run");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  gs::Problem pb = make_problem(N, y0, params, t0, t1, rtol, atol, K, saveat, opt);
+  pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
+  rc = set_tape(pb, d, N, workspace, workspace_bytes);
+  if (rc) return rc;
+  pb.queue = static_cast<unsigned int*>(workspace);
+  pb.dLdy = dLdy; pb.dLdy0 = dLdy0; pb.dLdp = dLdparams;
+  const int kernel = opt->kernel == GS_KERNEL_AUTO ? GS_KERNEL_PERSISTENT : opt->kernel;
+  gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s};
+  if (!opt->reuse_tape) {
+    cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    pb.record = 1;
+    e = forward_of(system)(pb, c);
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+  }
+  pb.record = 0;
+  // the reverse pass takes its work-queue counter from header bytes [4, 8)
+  pb.queue = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(workspace) + 4);
+  if (kernel == GS_KERNEL_PERSISTENT) {
+    cudaError_t e0 = cudaMemsetAsync(pb.queue, 0, 4, s);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
+  }
+  cudaError_t e = reverse_of(system)(pb, c);
+  if (e != cudaSuccess) return cuda_fail(e, "reverse launch");
+  return GS_OK;
+}
+
+int gs_rhs(int32_t system, int32_t precision, int64_t M, const double* t, const double* y, const double* params,
+           const double* w, double* f, double* gy, double* gp, void* cuda_stream) {
+  int32_t d, p;
+  if (dims_of(system, &d, &p)) return fail(GS_ERR_INVALID, "unknown system id %d", system);
+  if (precision < 0 || precision > 1) return fail(GS_ERR_INVALID, "unknown precision %d", precision);
+  if (M < 0) return fail(GS_ERR_INVALID, "M < 0");
+  if (M == 0) return GS_OK;
+  if (!t || !y || (p > 0 && !params)) return fail(GS_ERR_INVALID, "t, y (and params) must not be NULL");
+  if ((gy || gp) && !w) return fail(GS_ERR_INVALID, "w must not be NULL when a VJP is requested");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e;
+  switch (system) {
+    case GS_SYS_ISOCHRONE: e = gs::rhs_isochrone(precision, M, t, y, params, w, f, gy, gp, s); break;
+    case GS_SYS_MW: e = gs::rhs_mw(precision, M, t, y, params, w, f, gy, gp, s); break;
+    case GS_SYS_PRECESSION: e = gs::rhs_precession(precision, M, t, y, params, w, f, gy, gp, s); break;
+    case GS_SYS_QUINTESSENCE: e = gs::rhs_quintessence(precision, M, t, y, params, w, f, gy, gp, s); break;
+    default: e = gs::rhs_loghalo(precision, M, t, y, params, w, f, gy, gp, s); break;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "rhs launch");
+  return GS_OK;
+}
+
+const char* gs_last_error(void) { return g_err.c_str(); }
+
+const char* gs_version(void) { return "gs-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

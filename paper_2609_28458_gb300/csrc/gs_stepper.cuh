@@ -1,0 +1,502 @@
+// Per-trajectory adaptive explicit Runge-Kutta integration as a step state machine, and the
+// discrete adjoint of one accepted step.
+//
+// One object of Traj holds a trajectory's private state (Sec. 2.4: state, stages and FSAL stage in
+// the thread's registers). init() loads a trajectory, attempt() makes one step attempt
+// (Appendix A: Eq. rk stages, Eq. errnorm norm, Eq. controller new step, Eq. dense outputs) and
+// finish() writes the status and step counts. The plain kernel runs init/attempt.../finish per
+// thread; the persistent kernel interleaves them so a lane that finishes takes new work at once.
+//
+// Precision (template F32):
+//  F32 = false: everything FP64.
+//  F32 = true : stage vectors, right-hand sides and dense outputs in FP32; the state is a
+//               compensated FP32 pair (hi + lo, updated with an error-free TwoSum); the squares of
+//               the scaled errors are accumulated in FP64; t is FP64 with Kahan compensation; h,
+//               the accept test and the step-size update are FP64, with the controller's power
+//               err^-beta1 taken in FP32 (it only scales a proposal clamped to [0.2, 5]).
+//
+// Readings where the paper is silent (the same as the CPU oracle's): Hairer-Norsett-Wanner starting
+// step with exponent 1/(nu+1); the last step is clipped to land on t1 when h(1+4eps) >= t1 - t;
+// h underflow when h < 16 eps max(|t|,|t1|); max_steps attempts; failures give NaN outputs.
+#pragma once
+#include <cfloat>
+#include <cstdint>
+#include <type_traits>
+
+#include "gs_systems.cuh"
+#include "gs_tableaux.cuh"
+
+namespace gs {
+
+enum : int32_t {
+  ST_MAX_STEPS = 1, ST_H_UNDERFLOW = 2, ST_NONFINITE = 4, ST_EMPTY = 8, ST_SAVEAT_OUTSIDE = 16,
+  ST_TAPE_OVERFLOW = 32
+};
+constexpr int32_t ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW;
+constexpr int kChunk = 32;  // accepted steps per tape chunk
+
+// Step tape: per accepted step the state at its start, t, tc, h and a last-step flag, in chunks of
+// kChunk slots taken from a pool with an atomic bump counter (no waits anywhere). Each chunk starts
+// with a 16-byte header holding the index of the trajectory's previous chunk, so the chunks of one
+// trajectory form a list walked backwards by the reverse pass from head[n].
+constexpr int kChunkHeader = 16;
+struct Tape {
+  unsigned char* pool;
+  long long pool_chunks;
+  long long chunk_bytes;
+  unsigned long long* pool_next;
+  int32_t* head;   // [N] last chunk of each trajectory (-1: none)
+  int32_t* n_rec;  // [N] accepted steps recorded (-1: the tape overflowed)
+};
+
+struct Problem {
+  long long N;
+  int32_t K, per_traj;
+  const double* y0;
+  const double* params;
+  const double* t0;
+  const double* t1;
+  const double* saveat;
+  double rtol, atol;
+  int32_t max_steps;
+  double safety, alpha_min, alpha_max, beta1, beta2, h0;
+  double* y_out;
+  int32_t* status;
+  int32_t* n_acc;
+  int32_t* n_rej;
+  int32_t record;
+  Tape tape;
+  unsigned int* queue;  // persistent kernel work counter
+  // adjoint
+  const double* dLdy;
+  double* dLdy0;
+  double* dLdp;
+};
+
+__device__ __forceinline__ double save_at(const Problem& pb, long long n, int k) {
+  return pb.per_traj ? pb.saveat[n * pb.K + k] : pb.saveat[k];
+}
+
+// An output time is used iff it lies in [t0, t1] and does not decrease.
+__device__ __forceinline__ bool save_valid(const Problem& pb, long long n, int k, double t0, double t1) {
+  const double s = save_at(pb, n, k);
+  return s >= t0 && s <= t1 && (k == 0 || s >= save_at(pb, n, k - 1));
+}
+
+template <class R>
+__device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
+  s = a + b;
+  const R bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <template <class> class SysT, class Tab, bool F32>
+struct Traj {
+  using R = typename std::conditional<F32, float, double>::type;
+  using Sys = SysT<R>;
+  static constexpr int D = Sys::D, NP = Sys::P, S = Tab::S;
+  static constexpr int NPA = NP > 0 ? NP : 1;
+  static constexpr int DL = F32 ? D : 1;
+  // slot layout: F64: y[D] | t, tc, h, flag ; F32: hi[D] lo[D] (floats) | t, tc, h, flag
+  static constexpr int kSlotBytes = (F32 ? 8 * D : 8 * D) + 32;
+
+  R y[D];     // state (F64) / high part (F32)
+  R ylo[DL];  // low part (F32)
+  R k1[D];    // f(t, y): the first stage of the next attempt
+  R p[NPA];
+  double t, tc, h, t0, t1, err_prev;
+  float atolf, rtolf, lerr_prev;  // F32: tolerances and log2 of the previous error
+  long long n;
+  int32_t kk, nacc, nrej, status, chunk;
+  bool done, failed, rec_ok;
+
+  __device__ __forceinline__ R stage_time(double ts) const { return R(ts); }
+
+  __device__ __forceinline__ double yval(int i) const {
+    if constexpr (F32) return double(y[i]) + double(ylo[i]);
+    else return y[i];
+  }
+
+  __device__ void write_out(const Problem& pb, int k, const R* hi, const R* lo) {
+    double* o = pb.y_out + (n * pb.K + k) * D;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      if constexpr (F32) o[i] = double(hi[i]) + double(lo[i]);
+      else o[i] = hi[i];
+    }
+  }
+  __device__ void write_nan(const Problem& pb, int k) {
+    double* o = pb.y_out + (n * pb.K + k) * D;
+#pragma unroll
+    for (int i = 0; i < D; i++) o[i] = __longlong_as_double(0x7ff8000000000000LL);
+  }
+
+  // Hairer, Norsett & Wanner I, Sec. II.4 starting step (FP64 norms).
+  __device__ double initial_step(const Problem& pb) {
+    double sc[D];
+    double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const double yi = yval(i);
+      sc[i] = pb.atol + pb.rtol * fabs(yi);
+      const double r0 = yi / sc[i];
+      d0 += r0 * r0;
+      const double r1 = double(k1[i]) / sc[i];
+      d1 += r1 * r1;
+    }
+    d0 = sqrt(d0 / D);
+    d1 = sqrt(d1 / D);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * (d0 / d1);
+    if (h0 > t1 - t0) h0 = t1 - t0;
+    R y1[D], f1[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      if constexpr (F32) y1[i] = y[i] + (ylo[i] + R(h0) * k1[i]);
+      else y1[i] = y[i] + h0 * k1[i];
+    }
+    Sys::f(stage_time(t0 + h0), y1, p, f1);
+    double d2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const double r = (double(f1[i]) - double(k1[i])) / sc[i];
+      d2 += r * r;
+    }
+    d2 = sqrt(d2 / D) / h0;
+    const double dm = d1 > d2 ? d1 : d2;
+    const double h1 = (dm <= 1e-15) ? (h0 * 1e-3 > 1e-6 ? h0 * 1e-3 : 1e-6) : pow(0.01 / dm, 1.0 / (Tab::ORDER + 1));
+    double hh = 100.0 * h0 < h1 ? 100.0 * h0 : h1;
+    if (hh > t1 - t0) hh = t1 - t0;
+    return hh;
+  }
+
+  __device__ void init(const Problem& pb, long long traj) {
+    n = traj;
+    status = 0; nacc = 0; nrej = 0; kk = 0;
+    done = false; failed = false; rec_ok = true; chunk = -1;
+    t0 = pb.t0[n];
+    t1 = pb.t1[n];
+    bool fin = isfinite(t0) && isfinite(t1);
+    double y0d[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      y0d[i] = pb.y0[n * D + i];
+      fin = fin && isfinite(y0d[i]);
+      if constexpr (F32) {
+        y[i] = float(y0d[i]);
+        ylo[i] = float(y0d[i] - double(y[i]));
+      } else {
+        y[i] = y0d[i];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; q++) {
+      const double pv = pb.params[n * NP + q];
+      fin = fin && isfinite(pv);
+      p[q] = R(pv);
+    }
+    if (NP == 0) p[0] = R(0);
+    if (!fin) {
+      status = ST_NONFINITE;
+      failed = true;
+      done = true;
+      return;
+    }
+    if (!(t1 > t0)) {  // empty or reversed interval: every output is y0
+      status = ST_EMPTY;
+      for (int k = 0; k < pb.K; k++) {
+        double* o = pb.y_out + (n * pb.K + k) * D;
+#pragma unroll
+        for (int i = 0; i < D; i++) o[i] = y0d[i];
+      }
+      done = true;
+      return;
+    }
+    for (int k = 0; k < pb.K; k++) {
+      if (!save_valid(pb, n, k, t0, t1)) {
+        status |= ST_SAVEAT_OUTSIDE;
+        write_nan(pb, k);
+      }
+    }
+    while (kk < pb.K && (!save_valid(pb, n, kk, t0, t1) || save_at(pb, n, kk) == t0)) {
+      if (save_valid(pb, n, kk, t0, t1)) {
+        double* o = pb.y_out + (n * pb.K + kk) * D;
+#pragma unroll
+        for (int i = 0; i < D; i++) o[i] = y0d[i];
+      }
+      kk++;
+    }
+    Sys::f(stage_time(t0), y, p, k1);
+    t = t0;
+    tc = 0.0;
+    err_prev = 1.0;
+    lerr_prev = 0.0f;
+    atolf = float(pb.atol);
+    rtolf = float(pb.rtol);
+    h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step(pb);
+  }
+
+  // Stages of one step of length hh from (tt, y): Eq. rk. k[0] = k1 on entry.
+  // Y[j] receives the state at which stage j was evaluated (Y[0] = y).
+  __device__ __forceinline__ void stages(double tt, double hh, R (*k)[D], R (*Y)[D], int nst) const {
+    const R hr = R(hh);
+#pragma unroll
+    for (int i = 0; i < D; i++) { k[0][i] = k1[i]; if (Y) Y[0][i] = y[i]; }
+#pragma unroll
+    for (int j = 1; j < S; j++) {
+      if (j < nst) {
+        R Yj[D];
+#pragma unroll
+        for (int i = 0; i < D; i++) {
+          R acc = R(0);
+#pragma unroll
+          for (int l = 0; l < j; l++)
+            if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
+          if constexpr (F32) Yj[i] = y[i] + (ylo[i] + hr * acc);
+          else Yj[i] = y[i] + hh * acc;
+          if (Y) Y[j][i] = Yj[i];
+        }
+        Sys::f(stage_time(tt + Tab::c(j) * hh), Yj, p, k[j]);
+      }
+    }
+  }
+
+  // Solution at tt + sig*hh inside the accepted step just taken (Eq. dense; Verner 7: shortened
+  // step from the start of the step). k holds the step's stages.
+  __device__ void dense_point(double tt, double hh, double sig, R (*k)[D], R* hi, R* lo) const {
+    if constexpr (Tab::DENSE_POLY) {
+      R w[S];
+      Tab::dense(R(sig), w);
+      const R hr = R(hh);
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        R acc = R(0);
+#pragma unroll
+        for (int j = 0; j < S; j++) acc = acc + w[j] * k[j][i];
+        if constexpr (F32) { hi[i] = y[i]; lo[i] = ylo[i] + hr * acc; }
+        else { hi[i] = y[i] + hh * acc; lo[i] = R(0); }
+      }
+    } else {
+      R ks[S][D];
+      const double hs = sig * hh;
+      stages(tt, hs, ks, nullptr, Tab::NREV);
+      const R hr = R(hs);
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        R acc = R(0);
+#pragma unroll
+        for (int j = 0; j < Tab::NREV; j++)
+          if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * ks[j][i];
+        if constexpr (F32) { hi[i] = y[i]; lo[i] = ylo[i] + hr * acc; }
+        else { hi[i] = y[i] + hs * acc; lo[i] = R(0); }
+      }
+    }
+  }
+
+  __device__ void record_slot(const Problem& pb, bool last) {
+    const int a = nacc - 1;  // index of the step just accepted
+    if (!rec_ok) return;
+    const int o = a % kChunk;
+    if (o == 0) {
+      const unsigned long long idx = atomicAdd(pb.tape.pool_next, 1ULL);
+      if (idx >= (unsigned long long)pb.tape.pool_chunks) { rec_ok = false; return; }
+      long long* hdr = reinterpret_cast<long long*>(pb.tape.pool + (long long)idx * pb.tape.chunk_bytes);
+      hdr[0] = chunk;
+      chunk = int32_t(idx);
+    }
+    unsigned char* slot = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader +
+                          (long long)o * kSlotBytes;
+    if constexpr (F32) {
+      float* f = reinterpret_cast<float*>(slot);
+#pragma unroll
+      for (int i = 0; i < D; i++) { f[i] = y[i]; f[D + i] = ylo[i]; }
+    } else {
+      double* f = reinterpret_cast<double*>(slot);
+#pragma unroll
+      for (int i = 0; i < D; i++) f[i] = y[i];
+    }
+    double* tail = reinterpret_cast<double*>(slot + 8 * D);
+    tail[0] = t; tail[1] = tc; tail[2] = h; tail[3] = last ? 1.0 : 0.0;
+  }
+
+  __device__ void fail(int32_t bit) {
+    status |= bit;
+    failed = true;
+    done = true;
+  }
+
+  // One step attempt.
+  __device__ void attempt(const Problem& pb) {
+    const double rem = (t1 - t) + tc;
+    if (rem <= 0.0) {  // the interval closed without a final step: remaining outputs are y
+      while (kk < pb.K) {
+        if (save_valid(pb, n, kk, t0, t1)) write_out(pb, kk, y, ylo);
+        kk++;
+      }
+      done = true;
+      return;
+    }
+    if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+    bool last = false;
+    if (h * (1.0 + 4.0 * DBL_EPSILON) >= rem) {
+      h = rem;
+      last = true;
+    } else {
+      const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
+      if (!(h >= 16.0 * DBL_EPSILON * tm)) { fail(isnan(h) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW); return; }
+    }
+    R k[S][D];
+    R Ylast[D];
+    const R hr = R(h);
+    // stages 2..S (the last one is the new state for FSAL pairs)
+#pragma unroll
+    for (int i = 0; i < D; i++) k[0][i] = k1[i];
+#pragma unroll
+    for (int j = 1; j < S; j++) {
+      R Yj[D];
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        R acc = R(0);
+#pragma unroll
+        for (int l = 0; l < j; l++)
+          if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
+        if constexpr (F32) Yj[i] = y[i] + (ylo[i] + hr * acc);
+        else Yj[i] = y[i] + h * acc;
+        if (j == S - 1) Ylast[i] = Yj[i];
+      }
+      Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
+    }
+    // new state: increments h sum b_j k_j
+    R ynew[D], ynlo[DL];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      if constexpr (Tab::FSAL && !F32) {
+        ynew[i] = Ylast[i];
+      } else {
+        R acc = R(0);
+#pragma unroll
+        for (int j = 0; j < S; j++)
+          if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * k[j][i];
+        if constexpr (F32) {
+          two_sum(y[i], ylo[i] + hr * acc, ynew[i], ynlo[i]);
+        } else {
+          ynew[i] = y[i] + h * acc;
+        }
+      }
+    }
+    // error estimate e = h sum (b_j - bhat_j) k_j and its scaled RMS norm, Eq. errnorm:
+    // ||e|| = sqrt(sq / d), sq = sum_i (e_i / s_i)^2 accumulated in FP64 in both precisions
+    double sq = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      R acc = R(0);
+#pragma unroll
+      for (int j = 0; j < S; j++)
+        if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * k[j][i];
+      if constexpr (F32) {
+        const R e = hr * acc;
+        const R a = fabsf(y[i]), b = fabsf(ynew[i]);
+        const R sc = atolf + rtolf * (a > b ? a : b);
+        const double r = double(__fdividef(e, sc));
+        sq += r * r;
+      } else {
+        const double e = h * acc;
+        const double a = fabs(y[i]), b = fabs(ynew[i]);
+        const double sc = pb.atol + pb.rtol * (a > b ? a : b);
+        const double r = e / sc;
+        sq += r * r;
+      }
+    }
+    // accept iff ||e|| <= 1; new step h * clamp(safety ||e||^-beta1 err_prev^beta2, alpha_min,
+    // alpha_max) after accepted and rejected attempts alike (Eq. controller; PI form for beta2 != 0)
+    bool accept;
+    double err = 0.0;
+    float lerr = 0.0f;
+    if constexpr (F32) {
+      accept = sq <= double(D);
+      lerr = 0.5f * (__log2f(float(sq)) - log2f(float(D)));  // log2 ||e||
+    } else {
+      err = sqrt(sq / D);
+      accept = err <= 1.0;
+    }
+    if (accept) {
+      nacc += 1;
+      if (pb.record) record_slot(pb, last);
+      // outputs inside (t, t + h]
+      while (kk < pb.K) {
+        if (!save_valid(pb, n, kk, t0, t1)) { kk++; continue; }
+        const double sv = save_at(pb, n, kk);
+        const double dk = (sv - t) + tc;
+        if (last && sv == t1) {
+          write_out(pb, kk, ynew, F32 ? ynlo : ynew);
+        } else if (last || dk <= h) {
+          double sig = dk / h;
+          if (sig > 1.0) sig = 1.0;
+          if (sig < 0.0) sig = 0.0;
+          R hi[D], lo[D];
+          dense_point(t, h, sig, k, hi, lo);
+          write_out(pb, kk, hi, lo);
+        } else {
+          break;
+        }
+        kk++;
+      }
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        y[i] = ynew[i];
+        if constexpr (F32) ylo[i] = ynlo[i];
+        if constexpr (Tab::FSAL) k1[i] = k[S - 1][i];
+      }
+      if (last) {
+        t = t1; tc = 0.0; done = true;
+      } else {
+        const double yk = h - tc;  // Kahan summation of the time
+        const double tn = t + yk;
+        tc = (tn - t) - yk;
+        t = tn;
+        if constexpr (!Tab::FSAL) Sys::f(stage_time(t), y, p, k1);
+        h = h * factor(pb, err, lerr);
+        if constexpr (F32) lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;  // log2(1e-4)
+        else err_prev = err > 1e-4 ? err : 1e-4;
+      }
+    } else {
+      nrej += 1;
+      const bool bad = F32 ? isnan(sq) : isnan(err);
+      h = h * (bad ? pb.alpha_min : factor(pb, err, lerr));
+      err_prev = 1.0;
+      lerr_prev = 0.0f;
+    }
+  }
+
+  // safety * ||e||^-beta1 * err_prev^beta2 clamped to [alpha_min, alpha_max]. F32: the power is
+  // taken in FP32 from log2 ||e|| (err = 0 gives alpha_max, err = inf gives alpha_min).
+  __device__ __forceinline__ double factor(const Problem& pb, double err, float lerr) const {
+    if constexpr (F32) {
+      float lf = -float(pb.beta1) * lerr;
+      if (pb.beta2 != 0.0) lf += float(pb.beta2) * lerr_prev;
+      float fac = float(pb.safety) * exp2f(lf);
+      fac = fminf(fmaxf(fac, float(pb.alpha_min)), float(pb.alpha_max));
+      return double(fac);
+    } else {
+      double fac = pb.safety * pow(err, -pb.beta1) * (pb.beta2 != 0.0 ? pow(err_prev, pb.beta2) : 1.0);
+      if (fac > pb.alpha_max) fac = pb.alpha_max;
+      if (fac < pb.alpha_min) fac = pb.alpha_min;
+      return fac;
+    }
+  }
+
+  __device__ void finish(const Problem& pb) {
+    if (failed) {
+      for (int k = 0; k < pb.K; k++) write_nan(pb, k);
+    }
+    if (pb.record) {
+      if (!rec_ok) status |= ST_TAPE_OVERFLOW;
+      pb.tape.n_rec[n] = rec_ok ? nacc : -1;
+      pb.tape.head[n] = chunk;
+    }
+    pb.status[n] = status;
+    pb.n_acc[n] = nacc;
+    pb.n_rej[n] = nrej;
+  }
+};
+
+}  // namespace gs

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/gs.h; host-side
+argument checks reject bad calls before any launch (CPU only: no kernel runs here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2609_28458_gb300 import _abi
+from paper_2609_28458_gb300 import build as gsbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gsbuild.build()
+    return _abi.lib()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert set(names) == set(_abi.EXPORTS), names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_dims_and_defaults(lib):
+    assert [_abi.dims(s) for s in ("isochrone", "mw", "precession", "quintessence", "loghalo")] == \
+        [(6, 0), (6, 4), (9, 3), (3, 4), (6, 3)]
+    o = _abi.options()
+    assert (o.method, o.precision, o.max_steps, o.safety, o.alpha_min, o.alpha_max) == (0, 0, 1000000, 0.9, 0.2, 5.0)
+    assert lib.gs_version().decode().startswith("gs-gb300")
+
+
+def test_host_checks_reject_before_launch(lib):
+    o = _abi.options()
+    d, p = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.gs_dims(99, ctypes.byref(d), ctypes.byref(p)) == _abi.GS_ERR_INVALID
+    assert "unknown system" in lib.gs_last_error().decode()
+    # N = 0 is a valid no-op
+    assert lib.gs_solve(0, 0, None, None, None, None, 1e-6, 1e-6, 0, None, ctypes.byref(o), None, None, None, None,
+                        None, 0, None) == _abi.GS_OK
+    # null inputs with N > 0
+    assert lib.gs_solve(0, 4, None, None, None, None, 1e-6, 1e-6, 1, None, ctypes.byref(o), None, None, None, None,
+                        None, 0, None) == _abi.GS_ERR_INVALID
+    # bad tolerances / options
+    fake = ctypes.c_void_p(256)
+    assert lib.gs_solve(0, 4, fake, None, fake, fake, -1.0, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
+                        None, 0, None) == _abi.GS_ERR_INVALID
+    o.method = 7
+    assert lib.gs_solve(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
+                        None, 0, None) == _abi.GS_ERR_INVALID
+    o = _abi.options(kernel="persistent")
+    assert lib.gs_solve(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
+                        None, 0, None) == _abi.GS_ERR_WORKSPACE
+    # vjp needs a tape workspace
+    o = _abi.options()
+    assert lib.gs_vjp(1, 4, fake, fake, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake, fake,
+                      fake, fake, None, 0, None) == _abi.GS_ERR_WORKSPACE
+
+
+def test_workspace_sizes(lib):
+    o = _abi.options()
+    small = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 0, 0.0)
+    big = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 1, 500.0)
+    assert small >= 256 and big > small
+    # a tape chunk holds 32 slots of (8 d + 32) bytes behind a 16-byte header
+    assert (big - small) == (1000 * (16 + 1) + 1) * (16 + 32 * (8 * 6 + 32))

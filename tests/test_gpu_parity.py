@@ -1,0 +1,166 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances:
+* FP64, isochrone workload (4096 orbits, Tsit5, rtol 1e-10, atol 1e-12, 11 outputs): every output
+  of every trajectory within 1e-9 relative of the oracle's same-algorithm solve.
+* FP64, other systems: trajectories whose accepted/rejected step counts equal the oracle's (the
+  same step sequence) agree to 1e-10 relative; a trajectory whose sequence differs (a rounding-level
+  difference flipped one accept test) still agrees to 50 x rtol, and such flips must be rare.
+* FP32 stages: the error against the converged oracle (Verner 7, rtol 1e-12) meets the paper's
+  budget in the paper's measure (Eq. accept): P99 <= 1e-4 for orbits (Eq. st-fwderr) and for
+  distances in c/H0 (Sec. 4.2).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import gpu_solve, rel_err
+from paper_2609_28458_gb300 import metrics as M
+from paper_2609_28458_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_solve(e, method=None, rtol=None, atol=None, **kw):
+    return O.solve(e.system, e.y0, e.params, e.t0, e.t1, e.saveat, e.rtol if rtol is None else rtol,
+                   e.atol if atol is None else atol, method=method or e.method, **kw)
+
+
+@pytest.mark.parametrize("kernel", ["plain", "persistent"])
+def test_isochrone_workload_fp64_within_1e9(kernel):
+    e = W.isochrone(n=4096, seed=0)
+    ref = oracle_solve(e)
+    g = gpu_solve(e, kernel=kernel)
+    assert np.all(g["status"] == 0) and np.all(ref["status"] == 0)
+    err = rel_err(g["y"], ref["y"])
+    assert err.max() <= 1e-9, (err.max(), np.argmax(err))
+    same = (g["n_accept"] == ref["n_accept"]) & (g["n_reject"] == ref["n_reject"])
+    assert same.mean() > 0.99
+
+
+CASES = [
+    ("mw", lambda: W.mw(n=256, seed=21, t1=1500.0, rtol=1e-8), "tsit5"),
+    ("mw", lambda: W.mw(n=256, seed=22, t1=1500.0, rtol=1e-8), "dopri5"),
+    ("mw", lambda: W.mw(n=128, seed=23, t1=1500.0, rtol=1e-8), "vern7"),
+    ("precession", lambda: W.precession(n=128, seed=24, paper_interval=True, rtol=1e-9), "vern7"),
+    ("precession", lambda: W.precession(n=256, seed=25, method="tsit5", rtol=1e-9), "tsit5"),
+    ("quintessence", lambda: W.quintessence(n=256, seed=26, rtol=1e-8), "tsit5"),
+    ("quintessence", lambda: W.quintessence(n=256, seed=27, rtol=1e-8, dense=True), "dopri5"),
+    ("quintessence", lambda: W.quintessence(n=128, seed=28, rtol=1e-8), "vern7"),
+    ("loghalo", lambda: W.loghalo(n=256, seed=29, rtol=1e-8), "tsit5"),
+    ("isochrone", lambda: W.isochrone(n=256, seed=30), "vern7"),
+]
+
+
+@pytest.mark.parametrize("system,gen,method", CASES)
+@pytest.mark.parametrize("kernel", ["plain", "persistent"])
+def test_fp64_same_algorithm_parity(system, gen, method, kernel):
+    e = gen()
+    ref = oracle_solve(e, method=method)
+    g = gpu_solve(e, method=method, kernel=kernel)
+    assert np.array_equal(g["status"], ref["status"])
+    ok = (ref["status"] & O.ST_EMPTY_INTERVAL) == 0
+    same = (g["n_accept"] == ref["n_accept"]) & (g["n_reject"] == ref["n_reject"])
+    err = rel_err(g["y"], ref["y"])
+    assert same[ok].mean() >= 0.9, same.mean()
+    assert err[same & ok].max() <= 1e-10, err[same & ok].max()
+    assert err[ok].max() <= 50 * e.rtol, err[ok].max()
+    empty = ~ok
+    assert np.array_equal(g["y"][empty], ref["y"][empty])
+
+
+def test_persistent_kernel_is_bitwise_equal_to_plain():
+    for prec in ("fp64", "fp32"):
+        e = W.mw(n=3000, seed=31, t1=1000.0)
+        a = gpu_solve(e, precision=prec, kernel="plain")
+        b = gpu_solve(e, precision=prec, kernel="persistent")
+        for k in ("y", "status", "n_accept", "n_reject"):
+            assert np.array_equal(a[k], b[k]), (prec, k)
+
+
+def _converged(e, method="vern7"):
+    return oracle_solve(e, method=method, rtol=1e-12, atol=1e-12 if e.system != "quintessence" else 1e-14)
+
+
+@pytest.mark.parametrize("kernel", ["plain", "persistent"])
+def test_mw_meets_orbit_budget_at_searched_tolerance(kernel):
+    """Over 3 Gyr the workload's quoted rtol 3e-7 gives P99 ~ 1e-3 (outside the 1e-4 budget); the
+    quarter-decade search of Appendix A selects 3.16e-8 (FP32 stages) and 5.62e-8 (FP64). Checked
+    here one grid step tighter, on another draw."""
+    e = W.mw(n=1024, seed=32)
+    ref = _converged(e)
+    rE, vE = M.orbit_scales("mw", e.y0, e.params)
+    for prec, rtol in (("fp32", 1.78e-8), ("fp64", 3.16e-8)):
+        g = gpu_solve(e, precision=prec, kernel=kernel, rtol=rtol, atol=rtol)
+        assert np.all(g["status"] == 0)
+        err = M.orbit_error(g["y"][:, -1], ref["y"][:, -1], rE, vE)
+        assert M.accepted(err, 1e-4), (prec, M.p99(err), err.max())
+
+
+def test_fp32_stages_close_to_fp64_at_same_tolerance():
+    """The FP32-stage solve differs from the FP64 solve of the same tolerance by much less than the
+    budget: precision adds at most a small fraction to the truncation error."""
+    e = W.mw(n=2048, seed=37)
+    rE, vE = M.orbit_scales("mw", e.y0, e.params)
+    a = gpu_solve(e, precision="fp32", kernel="persistent", rtol=3.16e-8, atol=3.16e-8)
+    b = gpu_solve(e, precision="fp64", kernel="persistent", rtol=3.16e-8, atol=3.16e-8)
+    err = M.orbit_error(a["y"][:, -1], b["y"][:, -1], rE, vE)
+    assert M.p99(err) <= 1e-4, M.p99(err)
+
+
+def test_quintessence_fp32_stages_meet_distance_budget():
+    e = W.quintessence(n=1024, seed=33, rtol=1e-6)
+    ref = _converged(e, method="tsit5")
+    for method in ("tsit5", "dopri5"):
+        g = gpu_solve(e, method=method, precision="fp32")
+        assert np.all(g["status"] == 0)
+        err = M.distance_error(g["y"], ref["y"], e.params, e.saveat)
+        assert M.accepted(err, 1e-4), (method, M.p99(err))
+
+
+def test_precession_fp64_meets_angle_budget():
+    e = W.precession(n=512, seed=34)
+    ref = _converged(e)
+    g = gpu_solve(e, kernel="persistent")
+    err = M.precession_error(g["y"][:, -1], ref["y"][:, -1])
+    assert M.accepted(err, 2e-7), M.p99(err)
+
+
+def test_status_codes_and_edge_cases():
+    e = W.isochrone(n=6, seed=17)
+    e.y0[1, 2] = np.nan
+    e.t1[2] = 0.0
+    sv = np.stack([e.saveat] * 6)
+    sv[3, 10] = 150.0
+    sv[4, 6] = 45.0
+    e.saveat = sv
+    for kernel in ("plain", "persistent"):
+        ref = oracle_solve(e, rtol=1e-8, atol=1e-8)
+        g = gpu_solve(e, rtol=1e-8, atol=1e-8, kernel=kernel)
+        assert np.array_equal(g["status"], ref["status"])
+        assert np.array_equal(np.isnan(g["y"]), np.isnan(ref["y"]))
+        assert np.array_equal(g["y"][2], ref["y"][2])
+        ref = oracle_solve(e, rtol=1e-8, atol=1e-8, max_steps=20)
+        g = gpu_solve(e, rtol=1e-8, atol=1e-8, kernel=kernel, max_steps=20)
+        assert np.array_equal(g["status"], ref["status"])
+        assert np.array_equal(g["n_accept"] + g["n_reject"], ref["n_accept"] + ref["n_reject"])
+
+
+def test_outputs_at_t0_and_t1_are_exact_states():
+    e = W.isochrone(n=64, seed=35)
+    g = gpu_solve(e)
+    assert np.array_equal(g["y"][:, 0], e.y0)
+    ref = oracle_solve(e)
+    assert rel_err(g["y"][:, -1:], ref["y"][:, -1:]).max() <= 1e-9
+
+
+def test_empty_ensemble_and_no_outputs():
+    e = W.mw(n=8, seed=36, t1=100.0)
+    e0 = e.subset(np.arange(0))
+    g = gpu_solve(e0)
+    assert g["y"].shape == (0, 1, 6)
+    e.saveat = np.zeros(0)
+    g = gpu_solve(e)
+    ref = oracle_solve(e)
+    assert g["y"].shape == (8, 0, 6)
+    assert np.array_equal(g["n_accept"], ref["n_accept"]) or np.all(np.abs(g["n_accept"] - ref["n_accept"]) <= 1)
