@@ -51,8 +51,11 @@ typedef enum { GS_TSIT5 = 0, GS_DOPRI5 = 1, GS_VERN7 = 2 } gs_method;
 /* GS_FP64: every operation in FP64.
  * GS_FP32_STAGES: stage and right-hand-side arithmetic in FP32, the state kept as a compensated
  *   FP32 pair, the error-norm accumulation, the time (compensated summation) and the step-size
- *   controller in FP64. */
-typedef enum { GS_FP64 = 0, GS_FP32_STAGES = 1 } gs_precision;
+ *   controller in FP64.
+ * GS_FP32_DF: as GS_FP32_STAGES, but the time is an unevaluated FP32 pair (>= 48 significant bits,
+ *   advanced error-free), the step length is the FP32 number the stages use, and the norm
+ *   accumulation and controller run in FP32: the attempt loop issues no FP64 instruction. */
+typedef enum { GS_FP64 = 0, GS_FP32_STAGES = 1, GS_FP32_DF = 2 } gs_precision;
 
 /* GS_KERNEL_PLAIN: one thread per trajectory for its whole solve (a warp waits for its slowest
  *   member, Appendix A, Eq. cost). GS_KERNEL_PERSISTENT: persistent CTAs whose lanes take the next
@@ -126,7 +129,9 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
  *  With opt->reuse_tape, status, n_accept and n_reject are INPUTS: the arrays written by the
  *  recording gs_solve (status gains GS_ST_TAPE_OVERFLOW there); the forward solve is not re-run.
  *  The workspace holds the step tape: per accepted step the state at its start, its time and
- *  its length, in chunks taken from a pool by an atomic counter.
+ *  its length, in chunks taken from a pool by an atomic counter. Layout: a 256-byte header, int32
+ *  head[N] and n_rec[N] (each padded to 256 bytes), then chunks of 16 + 32 * slot bytes with
+ *  slot = roundup16(8 d) + 32; a trajectory with n accepted steps uses ceil(n / 32) chunks.
  */
 int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
            const double* t1, double rtol, double atol, int32_t K, const double* saveat,
@@ -144,7 +149,7 @@ size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options
 
 /* Evaluate f (Eq. ivp) and its vector-Jacobian products for M states, as the solver does:
  *  f [M,d] = f(t, y, theta);  gy [M,d] = J_y^T w;  gp [M,p] = J_theta^T w  (gy, gp may be NULL).
- *  precision selects the FP64 or FP32 instantiation. */
+ *  precision selects the FP64 (GS_FP64) or FP32 (the two FP32 modes) instantiation. */
 int gs_rhs(int32_t system, int32_t precision, int64_t M, const double* t, const double* y,
            const double* params, const double* w, double* f, double* gy, double* gp, void* cuda_stream);
 

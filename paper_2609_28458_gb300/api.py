@@ -77,7 +77,7 @@ def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None):
     d, _ = _abi.dims(system)
     opt = opt or _abi.options()
     fixed = _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 0, 0.0)
-    chunk = 16 + 32 * (8 * d + 32)
+    chunk = 16 + 32 * ((8 * d + 15) // 16 * 16 + 32)  # chunk header + 32 slots (gs.h)
     if n_accept is not None:
         chunks = int(((n_accept.to(torch.int64) + 31) // 32).sum().item()) + 1
         return fixed + chunks * chunk
@@ -142,6 +142,10 @@ def vjp(system, y0, params, t0, t1, saveat, rtol, atol, dLdy, method="tsit5", pr
             raise ValueError("reuse_tape needs the workspace the tape was recorded into")
         wsb = workspace.buf
     else:
+        if tape_nbytes is None and n_accept_hint is None:
+            # size the tape exactly from a forward solve with the same options (one extra solve)
+            n_accept_hint = solve(system, y0, params, t0, t1, saveat, rtol, atol, method=method, precision=precision,
+                                  kernel=kernel, **kw)["n_accept"]
         nbytes = tape_nbytes or tape_bytes(system, N, n_accept=n_accept_hint, steps_hint=steps_hint, opt=opt)
         wsb = _ws(dev, nbytes, workspace)
     res = dict(dLdy0=torch.empty((N, d), dtype=torch.float64, device=dev),

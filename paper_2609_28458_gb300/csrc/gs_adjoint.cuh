@@ -15,9 +15,10 @@
 
 namespace gs {
 
-template <template <class> class SysT, class Tab, bool F32>
+template <template <class> class SysT, class Tab, int PM>
 struct Adjoint {
-  using T = Traj<SysT, Tab, F32>;
+  using T = Traj<SysT, Tab, PM>;
+  static constexpr bool F32 = T::F32, DF = T::DF;
   using R = typename T::R;
   using Sys = typename T::Sys;
   static constexpr int D = T::D, NP = T::NP, S = Tab::S, NPA = T::NPA;
@@ -69,6 +70,7 @@ struct Adjoint {
 
   struct SlotView {
     double t, tc, h;
+    float th, tl, hf;  // PM 2: the time pair and FP32 step as recorded
     bool last;
   };
 
@@ -79,16 +81,36 @@ struct Adjoint {
     return int32_t(*reinterpret_cast<const long long*>(pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes));
   }
   __device__ static SlotView load_times(const unsigned char* s) {
-    const double* tail = reinterpret_cast<const double*>(s + 8 * D);
     SlotView v;
-    v.t = tail[0]; v.tc = tail[1]; v.h = tail[2]; v.last = tail[3] != 0.0;
+    if constexpr (DF) {
+      const float4 tail = *reinterpret_cast<const float4*>(s + T::kTailOff);
+      v.th = tail.x; v.tl = tail.y; v.hf = tail.z; v.last = tail.w != 0.0f;
+      v.t = double(v.th) + double(v.tl);
+      v.tc = 0.0;
+      v.h = double(v.hf);
+    } else {
+      const double* tail = reinterpret_cast<const double*>(s + T::kTailOff);
+      v.t = tail[0]; v.tc = tail[1]; v.h = tail[2]; v.last = tail[3] != 0.0;
+    }
     return v;
   }
   __device__ static void load_state(const unsigned char* s, T& tr) {
     if constexpr (F32) {
-      const float* f = reinterpret_cast<const float*>(s);
+      float v[2 * D];
+      if constexpr ((2 * D) % 4 == 0) {
+        const float4* f4 = reinterpret_cast<const float4*>(s);
 #pragma unroll
-      for (int i = 0; i < D; i++) { tr.y[i] = f[i]; tr.ylo[i] = f[D + i]; }
+        for (int q = 0; q < (2 * D) / 4; q++) {
+          const float4 a = f4[q];
+          v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+        }
+      } else {
+        const float2* f2 = reinterpret_cast<const float2*>(s);
+#pragma unroll
+        for (int q = 0; q < D; q++) { const float2 a = f2[q]; v[2 * q] = a.x; v[2 * q + 1] = a.y; }
+      }
+#pragma unroll
+      for (int i = 0; i < D; i++) { tr.y[i] = v[i]; tr.ylo[i] = v[D + i]; }
     } else {
       const double* f = reinterpret_cast<const double*>(s);
 #pragma unroll
@@ -96,8 +118,27 @@ struct Adjoint {
     }
   }
 
+  // the forward's test for an output inside a step, in the same arithmetic
   __device__ static bool inside(const SlotView& v, double sv) {
-    return v.last || ((sv - v.t) + v.tc) <= v.h;
+    if constexpr (DF) {
+      float svh, svl;
+      split_df(sv, svh, svl);
+      return v.last || ((svh - v.th) + (svl - v.tl)) <= v.hf;
+    } else {
+      return v.last || ((sv - v.t) + v.tc) <= v.h;
+    }
+  }
+  __device__ static R sigma(const SlotView& v, double sv) {
+    if constexpr (DF) {
+      float svh, svl;
+      split_df(sv, svh, svl);
+      return fminf(fmaxf(__fdividef((svh - v.th) + (svl - v.tl), v.hf), 0.0f), 1.0f);
+    } else {
+      double sg = ((sv - v.t) + v.tc) / v.h;
+      if (sg > 1.0) sg = 1.0;
+      if (sg < 0.0) sg = 0.0;
+      return R(sg);
+    }
   }
 
   // ---- reverse sweep of one trajectory as a state machine: init(), step() per recorded step,
@@ -198,13 +239,11 @@ struct Adjoint {
 #pragma unroll
         for (int i = 0; i < D; i++) ybar[i] += w[i];  // y(t1) is the new state itself
       } else {
-        double sig = ((sv - cur.t) + cur.tc) / cur.h;
-        if (sig > 1.0) sig = 1.0;
-        if (sig < 0.0) sig = 0.0;
+        const R sig = sigma(cur, sv);
         if constexpr (Tab::DENSE_POLY) {
           // y(t_k) = y + h sum_j b_j(sig) k_j
           R wd[S];
-          Tab::dense(R(sig), wd);
+          Tab::dense(sig, wd);
 #pragma unroll
           for (int j = 0; j < S; j++)
 #pragma unroll
@@ -214,7 +253,7 @@ struct Adjoint {
           for (int i = 0; i < D; i++) ydir[i] += w[i];
         } else {
           // Verner 7: y(t_k) = shortened step of length sig*h from (t, y)
-          const double hs = sig * cur.h;
+          const double hs = double(sig) * cur.h;
           R ks[S][D], Ys[S][D], kbs[S][D];
           tr.stages(cur.t, hs, ks, Ys, Tab::NREV);
           const R hsr = R(hs);

@@ -46,8 +46,8 @@ int order_of(int32_t method) { return method == GS_VERN7 ? 7 : 5; }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// bytes of one tape slot: state (8 d bytes in both precisions) + t, tc, h, flag
-long long slot_bytes(int32_t d) { return 8LL * d + 32; }
+// bytes of one tape slot: state (8 d bytes in every precision) padded to 16 bytes + a 32-byte tail
+long long slot_bytes(int32_t d) { return (8LL * d + 15) / 16 * 16 + 32; }
 long long chunk_bytes(int32_t d) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d); }
 
 // workspace: [0,256) header (queue counter at 0, pool counter at 8) | head[N] | n_rec[N] | pool
@@ -64,25 +64,30 @@ Layout layout(int64_t N) {
   return L;
 }
 
-typedef cudaError_t (*fwd_fn)(const gs::Problem&, const gs::LaunchCfg&);
-fwd_fn forward_of(int32_t sys) {
+typedef cudaError_t (*launch_fn)(const gs::Problem&, const gs::LaunchCfg&);
+#define GS_PICK(kind, sysname)                                  \
+  (method == GS_TSIT5 ? gs::kind##_##sysname##_Tsit5            \
+   : method == GS_DOPRI5 ? gs::kind##_##sysname##_Dopri5        \
+                         : gs::kind##_##sysname##_Vern7)
+launch_fn forward_of(int32_t sys, int32_t method) {
   switch (sys) {
-    case GS_SYS_ISOCHRONE: return gs::forward_isochrone;
-    case GS_SYS_MW: return gs::forward_mw;
-    case GS_SYS_PRECESSION: return gs::forward_precession;
-    case GS_SYS_QUINTESSENCE: return gs::forward_quintessence;
-    default: return gs::forward_loghalo;
+    case GS_SYS_ISOCHRONE: return GS_PICK(forward, isochrone);
+    case GS_SYS_MW: return GS_PICK(forward, mw);
+    case GS_SYS_PRECESSION: return GS_PICK(forward, precession);
+    case GS_SYS_QUINTESSENCE: return GS_PICK(forward, quintessence);
+    default: return GS_PICK(forward, loghalo);
   }
 }
-fwd_fn reverse_of(int32_t sys) {
+launch_fn reverse_of(int32_t sys, int32_t method) {
   switch (sys) {
-    case GS_SYS_ISOCHRONE: return gs::reverse_isochrone;
-    case GS_SYS_MW: return gs::reverse_mw;
-    case GS_SYS_PRECESSION: return gs::reverse_precession;
-    case GS_SYS_QUINTESSENCE: return gs::reverse_quintessence;
-    default: return gs::reverse_loghalo;
+    case GS_SYS_ISOCHRONE: return GS_PICK(reverse, isochrone);
+    case GS_SYS_MW: return GS_PICK(reverse, mw);
+    case GS_SYS_PRECESSION: return GS_PICK(reverse, precession);
+    case GS_SYS_QUINTESSENCE: return GS_PICK(reverse, quintessence);
+    default: return GS_PICK(reverse, loghalo);
   }
 }
+#undef GS_PICK
 
 int check_common(int32_t sys, int64_t N, const double* y0, const double* params, const double* t0,
                  const double* t1, double rtol, double atol, int32_t K, const double* saveat,
@@ -93,7 +98,7 @@ int check_common(int32_t sys, int64_t N, const double* y0, const double* params,
   if (N > (int64_t(1) << 31) - 4096) return fail(GS_ERR_INVALID, "N too large (max 2^31 - 4096)");
   if (K < 0) return fail(GS_ERR_INVALID, "K < 0");
   if (opt->method < 0 || opt->method > 2) return fail(GS_ERR_INVALID, "unknown method %d", opt->method);
-  if (opt->precision < 0 || opt->precision > 1) return fail(GS_ERR_INVALID, "unknown precision %d", opt->precision);
+  if (opt->precision < 0 || opt->precision > 2) return fail(GS_ERR_INVALID, "unknown precision %d", opt->precision);
   if (opt->kernel < 0 || opt->kernel > 2) return fail(GS_ERR_INVALID, "unknown kernel %d", opt->kernel);
   if (opt->block_size < 0 || opt->block_size > 128 || (opt->block_size % 32) != 0)
     return fail(GS_ERR_INVALID, "block_size must be 0 or a multiple of 32 up to 128");
@@ -124,6 +129,11 @@ gs::Problem make_problem(int64_t N, const double* y0, const double* params, cons
   pb.beta1 = opt->beta1 > 0.0 ? opt->beta1 : 1.0 / order_of(opt->method);
   pb.beta2 = opt->beta2;
   pb.h0 = opt->h0;
+  pb.fsafety = float(pb.safety);
+  pb.falpha_min = float(pb.alpha_min);
+  pb.falpha_max = float(pb.alpha_max);
+  pb.fbeta1 = float(pb.beta1);
+  pb.fbeta2 = float(pb.beta2);
   return pb;
 }
 
@@ -219,7 +229,7 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   }
   gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s};
-  cudaError_t e = forward_of(system)(pb, c);
+  cudaError_t e = forward_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   return GS_OK;
 }
@@ -249,7 +259,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     pb.record = 1;
-    e = forward_of(system)(pb, c);
+    e = forward_of(system, opt->method)(pb, c);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   }
   pb.record = 0;
@@ -259,7 +269,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
     cudaError_t e0 = cudaMemsetAsync(pb.queue, 0, 4, s);
     if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
   }
-  cudaError_t e = reverse_of(system)(pb, c);
+  cudaError_t e = reverse_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "reverse launch");
   return GS_OK;
 }
@@ -268,7 +278,7 @@ int gs_rhs(int32_t system, int32_t precision, int64_t M, const double* t, const 
            const double* w, double* f, double* gy, double* gp, void* cuda_stream) {
   int32_t d, p;
   if (dims_of(system, &d, &p)) return fail(GS_ERR_INVALID, "unknown system id %d", system);
-  if (precision < 0 || precision > 1) return fail(GS_ERR_INVALID, "unknown precision %d", precision);
+  if (precision < 0 || precision > 2) return fail(GS_ERR_INVALID, "unknown precision %d", precision);
   if (M < 0) return fail(GS_ERR_INVALID, "M < 0");
   if (M == 0) return GS_OK;
   if (!t || !y || (p > 0 && !params)) return fail(GS_ERR_INVALID, "t, y (and params) must not be NULL");

@@ -1,0 +1,8 @@
+// Kernel instantiations for the isochrone system with the Dopri5 pair (forward plain and persistent,
+// reverse plain and persistent, all precision modes).
+#include "gs_kernels.cuh"
+
+namespace gs {
+GS_DEFINE_METHOD(isochrone, Isochrone, Dopri5)
+
+}  // namespace gs

@@ -1,0 +1,8 @@
+// Kernel instantiations for the loghalo system with the Tsit5 pair (forward plain and persistent,
+// reverse plain and persistent, all precision modes).
+#include "gs_kernels.cuh"
+
+namespace gs {
+GS_DEFINE_METHOD(loghalo, LogHalo, Tsit5)
+GS_DEFINE_RHS(loghalo, LogHalo)
+}  // namespace gs

@@ -1,0 +1,8 @@
+// Kernel instantiations for the loghalo system with the Vern7 pair (forward plain and persistent,
+// reverse plain and persistent, all precision modes).
+#include "gs_kernels.cuh"
+
+namespace gs {
+GS_DEFINE_METHOD(loghalo, LogHalo, Vern7)
+
+}  // namespace gs

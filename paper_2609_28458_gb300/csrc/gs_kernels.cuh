@@ -1,5 +1,5 @@
-// Kernels of the ensemble solver and their launchers, instantiated once per system in the
-// gs_inst_*.cu translation units.
+// Kernels of the ensemble solver and their launchers, instantiated once per system and method in
+// the gs_inst_*.cu translation units.
 //
 //  k_plain    one thread per trajectory for its whole solve; a warp lasts as long as its slowest
 //             lane (the per-thread kernel of Sec. 2.4 / Appendix A, Eq. cost).
@@ -24,19 +24,30 @@ struct LaunchCfg {
   cudaStream_t stream;
 };
 
-template <template <class> class SysT, class Tab, bool F32>
+// Resident 128-thread blocks per SM requested from the register allocator (__launch_bounds__), for
+// 7-stage pairs on states of at most 6 components: the FP32-pipe forward fits 5 blocks
+// (96 registers), the FP64-control forward 4, the FP32 reverse 3 (<= 168), without spills. FP64,
+// Verner 7 and the 9-component precession state keep the compiler's choice.
+template <template <class> class SysT, class Tab, int PM>
+struct Occupancy {
+  static constexpr bool small = Tab::S <= 7 && SysT<float>::D <= 6;
+  static constexpr int fwd = (PM == 2 && small) ? 5 : (PM == 1 && small) ? 4 : 1;
+  static constexpr int rev = (PM != 0 && small) ? 3 : 1;
+};
+
+template <template <class> class SysT, class Tab, int PM>
 __global__ void __launch_bounds__(128) k_plain(const Problem pb) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= pb.N) return;
-  Traj<SysT, Tab, F32> tr;
+  Traj<SysT, Tab, PM> tr;
   tr.init(pb, n);
   while (!tr.done) tr.attempt(pb);
   tr.finish(pb);
 }
 
-template <template <class> class SysT, class Tab, bool F32>
-__global__ void __launch_bounds__(128) k_persist(const Problem pb) {
-  Traj<SysT, Tab, F32> tr;
+template <template <class> class SysT, class Tab, int PM>
+__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::fwd)) k_persist(const Problem pb) {
+  Traj<SysT, Tab, PM> tr;
   bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -67,19 +78,19 @@ __global__ void __launch_bounds__(128) k_persist(const Problem pb) {
   }
 }
 
-template <template <class> class SysT, class Tab, bool F32>
+template <template <class> class SysT, class Tab, int PM>
 __global__ void __launch_bounds__(128) k_reverse(const Problem pb) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= pb.N) return;
-  Adjoint<SysT, Tab, F32> adj;
+  Adjoint<SysT, Tab, PM> adj;
   adj.init(pb, n);
   while (!adj.done) adj.step(pb);
 }
 
 // Reverse sweeps from a work queue (counter pb.queue), lanes refilled as in k_persist.
-template <template <class> class SysT, class Tab, bool F32>
-__global__ void __launch_bounds__(128) k_reverse_persist(const Problem pb) {
-  Adjoint<SysT, Tab, F32> adj;
+template <template <class> class SysT, class Tab, int PM>
+__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_reverse_persist(const Problem pb) {
+  Adjoint<SysT, Tab, PM> adj;
   bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -156,11 +167,11 @@ inline int persistent_grid(K kernel, int block) {
   return per_sm * sm_count();
 }
 
-template <template <class> class SysT, class Tab, bool F32>
+template <template <class> class SysT, class Tab, int PM>
 cudaError_t launch_forward_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
   if (c.kernel == 2) {
-    auto kern = k_persist<SysT, Tab, F32>;
+    auto kern = k_persist<SysT, Tab, PM>;
     long long grid = persistent_grid(kern, block);
     const long long need = (pb.N + block - 1) / block;
     if (grid > need) grid = need;
@@ -168,16 +179,16 @@ cudaError_t launch_forward_t(const Problem& pb, const LaunchCfg& c) {
     kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
   } else {
     const long long grid = (pb.N + block - 1) / block;
-    k_plain<SysT, Tab, F32><<<unsigned(grid), block, 0, c.stream>>>(pb);
+    k_plain<SysT, Tab, PM><<<unsigned(grid), block, 0, c.stream>>>(pb);
   }
   return cudaGetLastError();
 }
 
-template <template <class> class SysT, class Tab, bool F32>
+template <template <class> class SysT, class Tab, int PM>
 cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
   if (c.kernel == 2) {
-    auto kern = k_reverse_persist<SysT, Tab, F32>;
+    auto kern = k_reverse_persist<SysT, Tab, PM>;
     long long grid = persistent_grid(kern, block);
     const long long need = (pb.N + block - 1) / block;
     if (grid > need) grid = need;
@@ -185,28 +196,25 @@ cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
     kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
   } else {
     const long long grid = (pb.N + block - 1) / block;
-    k_reverse<SysT, Tab, F32><<<unsigned(grid), block, 0, c.stream>>>(pb);
+    k_reverse<SysT, Tab, PM><<<unsigned(grid), block, 0, c.stream>>>(pb);
   }
   return cudaGetLastError();
 }
 
-template <template <class> class SysT>
-cudaError_t launch_forward(const Problem& pb, const LaunchCfg& c) {
-  const bool f32 = c.precision == 1;
-  switch (c.method) {
-    case 0: return f32 ? launch_forward_t<SysT, Tsit5, true>(pb, c) : launch_forward_t<SysT, Tsit5, false>(pb, c);
-    case 1: return f32 ? launch_forward_t<SysT, Dopri5, true>(pb, c) : launch_forward_t<SysT, Dopri5, false>(pb, c);
-    default: return f32 ? launch_forward_t<SysT, Vern7, true>(pb, c) : launch_forward_t<SysT, Vern7, false>(pb, c);
+template <template <class> class SysT, class Tab>
+cudaError_t launch_forward_m(const Problem& pb, const LaunchCfg& c) {
+  switch (c.precision) {
+    case 0: return launch_forward_t<SysT, Tab, 0>(pb, c);
+    case 1: return launch_forward_t<SysT, Tab, 1>(pb, c);
+    default: return launch_forward_t<SysT, Tab, 2>(pb, c);
   }
 }
-
-template <template <class> class SysT>
-cudaError_t launch_reverse(const Problem& pb, const LaunchCfg& c) {
-  const bool f32 = c.precision == 1;
-  switch (c.method) {
-    case 0: return f32 ? launch_reverse_t<SysT, Tsit5, true>(pb, c) : launch_reverse_t<SysT, Tsit5, false>(pb, c);
-    case 1: return f32 ? launch_reverse_t<SysT, Dopri5, true>(pb, c) : launch_reverse_t<SysT, Dopri5, false>(pb, c);
-    default: return f32 ? launch_reverse_t<SysT, Vern7, true>(pb, c) : launch_reverse_t<SysT, Vern7, false>(pb, c);
+template <template <class> class SysT, class Tab>
+cudaError_t launch_reverse_m(const Problem& pb, const LaunchCfg& c) {
+  switch (c.precision) {
+    case 0: return launch_reverse_t<SysT, Tab, 0>(pb, c);
+    case 1: return launch_reverse_t<SysT, Tab, 1>(pb, c);
+    default: return launch_reverse_t<SysT, Tab, 2>(pb, c);
   }
 }
 
@@ -216,24 +224,34 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
   const int block = 128;
   const long long grid = (M + block - 1) / block;
   if (grid == 0) return cudaSuccess;
-  if (precision == 1) k_rhs<SysT, true><<<unsigned(grid), block, 0, s>>>(M, t, y, p, w, f, gy, gp);
+  if (precision != 0) k_rhs<SysT, true><<<unsigned(grid), block, 0, s>>>(M, t, y, p, w, f, gy, gp);
   else k_rhs<SysT, false><<<unsigned(grid), block, 0, s>>>(M, t, y, p, w, f, gy, gp);
   return cudaGetLastError();
 }
 
-// per-system entry points defined in gs_inst_*.cu
-#define GS_DECLARE_SYSTEM(name)                                                                        \
-  cudaError_t forward_##name(const Problem& pb, const LaunchCfg& c);                                   \
-  cudaError_t reverse_##name(const Problem& pb, const LaunchCfg& c);                                   \
+// per-system, per-method entry points defined in gs_inst_<system>_<method>.cu, and the right-hand-side
+// evaluator of each system (in its Tsit5 unit)
+#define GS_DECLARE_METHOD(name, Tab)                                      \
+  cudaError_t forward_##name##_##Tab(const Problem& pb, const LaunchCfg& c); \
+  cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c);
+#define GS_DECLARE_SYSTEM(name)                                                                         \
+  GS_DECLARE_METHOD(name, Tsit5)                                                                        \
+  GS_DECLARE_METHOD(name, Dopri5)                                                                       \
+  GS_DECLARE_METHOD(name, Vern7)                                                                        \
   cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p, \
                          const double* w, double* f, double* gy, double* gp, cudaStream_t s);
 
-#define GS_DEFINE_SYSTEM(name, SysT)                                                                   \
-  cudaError_t forward_##name(const Problem& pb, const LaunchCfg& c) { return launch_forward<SysT>(pb, c); } \
-  cudaError_t reverse_##name(const Problem& pb, const LaunchCfg& c) { return launch_reverse<SysT>(pb, c); } \
-  cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p, \
-                         const double* w, double* f, double* gy, double* gp, cudaStream_t s) {         \
-    return launch_rhs<SysT>(precision, M, t, y, p, w, f, gy, gp, s);                                  \
+#define GS_DEFINE_METHOD(name, SysT, Tab)                                                                 \
+  cudaError_t forward_##name##_##Tab(const Problem& pb, const LaunchCfg& c) {                             \
+    return launch_forward_m<SysT, Tab>(pb, c);                                                           \
+  }                                                                                                      \
+  cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c) {                             \
+    return launch_reverse_m<SysT, Tab>(pb, c);                                                           \
+  }
+#define GS_DEFINE_RHS(name, SysT)                                                                         \
+  cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p,  \
+                         const double* w, double* f, double* gy, double* gp, cudaStream_t s) {           \
+    return launch_rhs<SysT>(precision, M, t, y, p, w, f, gy, gp, s);                                    \
   }
 
 }  // namespace gs

@@ -1,5 +1,4 @@
-// Per-trajectory adaptive explicit Runge-Kutta integration as a step state machine, and the
-// discrete adjoint of one accepted step.
+// Per-trajectory adaptive explicit Runge-Kutta integration as a step state machine.
 //
 // One object of Traj holds a trajectory's private state (Sec. 2.4: state, stages and FSAL stage in
 // the thread's registers). init() loads a trajectory, attempt() makes one step attempt
@@ -7,17 +6,23 @@
 // finish() writes the status and step counts. The plain kernel runs init/attempt.../finish per
 // thread; the persistent kernel interleaves them so a lane that finishes takes new work at once.
 //
-// Precision (template F32):
-//  F32 = false: everything FP64.
-//  F32 = true : stage vectors, right-hand sides and dense outputs in FP32; the state is a
-//               compensated FP32 pair (hi + lo, updated with an error-free TwoSum); the squares of
-//               the scaled errors are accumulated in FP64; t is FP64 with Kahan compensation; h,
-//               the accept test and the step-size update are FP64, with the controller's power
-//               err^-beta1 taken in FP32 (it only scales a proposal clamped to [0.2, 5]).
+// Precision mode PM:
+//  0  FP64: every operation in FP64.
+//  1  FP32 stages: stage vectors, right-hand sides and dense outputs in FP32; the state is a
+//     compensated FP32 pair (hi + lo, updated with an error-free TwoSum); the squares of the scaled
+//     errors are accumulated in FP64; t is FP64 with Kahan compensation; h, the accept test and the
+//     step-size update are FP64, with the controller's power taken in FP32 (it only scales a
+//     proposal that is then clamped to [alpha_min, alpha_max]).
+//  2  FP32 stages, FP32-pipe control: as 1, but the time is an unevaluated FP32 pair (th + tl,
+//     >= 48 significant bits, advanced by TwoSum), the step size the stages use is the FP32 step
+//     itself (so state and time advance by the same number), and the norm accumulation and the
+//     controller are FP32. No FP64 instruction is left in the attempt loop; FP64 on GB300 issues
+//     at a small fraction of the FP32 rate.
 //
 // Readings where the paper is silent (the same as the CPU oracle's): Hairer-Norsett-Wanner starting
 // step with exponent 1/(nu+1); the last step is clipped to land on t1 when h(1+4eps) >= t1 - t;
-// h underflow when h < 16 eps max(|t|,|t1|); max_steps attempts; failures give NaN outputs.
+// h underflow when h < 16 eps max(|t|,|t1|) (eps of the time representation); max_steps attempts;
+// failures give NaN outputs.
 #pragma once
 #include <cfloat>
 #include <cstdint>
@@ -35,10 +40,10 @@ enum : int32_t {
 constexpr int32_t ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW;
 constexpr int kChunk = 32;  // accepted steps per tape chunk
 
-// Step tape: per accepted step the state at its start, t, tc, h and a last-step flag, in chunks of
-// kChunk slots taken from a pool with an atomic bump counter (no waits anywhere). Each chunk starts
-// with a 16-byte header holding the index of the trajectory's previous chunk, so the chunks of one
-// trajectory form a list walked backwards by the reverse pass from head[n].
+// Step tape: per accepted step the state at its start, its time, its length and a last-step flag, in
+// chunks of kChunk slots taken from a pool with an atomic bump counter (no waits anywhere). Each
+// chunk starts with a 16-byte header holding the index of the trajectory's previous chunk, so the
+// chunks of one trajectory form a list walked backwards by the reverse pass from head[n].
 constexpr int kChunkHeader = 16;
 struct Tape {
   unsigned char* pool;
@@ -60,6 +65,7 @@ struct Problem {
   double rtol, atol;
   int32_t max_steps;
   double safety, alpha_min, alpha_max, beta1, beta2, h0;
+  float fsafety, falpha_min, falpha_max, fbeta1, fbeta2;  // FP32 copies for the FP32 controllers
   double* y_out;
   int32_t* status;
   int32_t* n_acc;
@@ -90,25 +96,50 @@ __device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <template <class> class SysT, class Tab, bool F32>
-struct Traj {
+// x = hi + lo with hi = fl32(x): an exact split of an FP64 number into an FP32 pair (48 bits).
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = float(x);
+  lo = float(x - double(hi));
+}
+
+constexpr float kEps48 = 3.5527136788005009e-15f;  // 2^-48: unit roundoff of an FP32 pair
+
+template <int PM>
+struct PrecTraits {
+  static constexpr bool F32 = PM != 0;
+  static constexpr bool DF = PM == 2;
   using R = typename std::conditional<F32, float, double>::type;
+};
+
+template <template <class> class SysT, class Tab, int PM>
+struct Traj {
+  static constexpr bool F32 = PrecTraits<PM>::F32;
+  static constexpr bool DF = PrecTraits<PM>::DF;
+  using R = typename PrecTraits<PM>::R;
   using Sys = SysT<R>;
   static constexpr int D = Sys::D, NP = Sys::P, S = Tab::S;
   static constexpr int NPA = NP > 0 ? NP : 1;
   static constexpr int DL = F32 ? D : 1;
-  // slot layout: F64: y[D] | t, tc, h, flag ; F32: hi[D] lo[D] (floats) | t, tc, h, flag
-  static constexpr int kSlotBytes = (F32 ? 8 * D : 8 * D) + 32;
+  // slot layout: y[D] as FP64 (PM 0) or hi[D] lo[D] as FP32 (PM 1, 2), padded to a multiple of
+  // 16 bytes, then a 32-byte tail: PM 0, 1: t, tc, h, flag (FP64); PM 2: th, tl, h, flag (FP32).
+  // Chunk headers and slots are multiples of 16 bytes, so every slot, state and tail is 16-byte
+  // aligned for the vector loads and stores below.
+  static constexpr int kTailOff = (8 * D + 15) / 16 * 16;
+  static constexpr int kSlotBytes = kTailOff + 32;
+  static_assert(kTailOff % 16 == 0 && kSlotBytes % 16 == 0 && kChunkHeader % 16 == 0,
+                "tape slots must stay 16-byte aligned");
+  static_assert(8 * D <= kTailOff, "state part of a slot overlaps its tail");
 
-  R y[D];     // state (F64) / high part (F32)
-  R ylo[DL];  // low part (F32)
+  R y[D];     // state (FP64) / high part (FP32)
+  R ylo[DL];  // low part (FP32)
   R k1[D];    // f(t, y): the first stage of the next attempt
   R p[NPA];
-  double t, tc, h, t0, t1, err_prev;
-  float atolf, rtolf, lerr_prev;  // F32: tolerances and log2 of the previous error
+  double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
+  float th, tl, hf, t1h, t1l, svh, svl;   // PM 2
+  float atolf, rtolf, lerr_prev;          // PM 1, 2
   long long n;
   int32_t kk, nacc, nrej, status, chunk;
-  bool done, failed, rec_ok;
+  bool done, failed, rec_ok, sv_ok;
 
   __device__ __forceinline__ R stage_time(double ts) const { return R(ts); }
 
@@ -129,6 +160,15 @@ struct Traj {
     double* o = pb.y_out + (n * pb.K + k) * D;
 #pragma unroll
     for (int i = 0; i < D; i++) o[i] = __longlong_as_double(0x7ff8000000000000LL);
+  }
+
+  // cache the output time of index kk (and whether it is used)
+  __device__ __forceinline__ void load_sv(const Problem& pb) {
+    if (kk < pb.K) {
+      sv_ok = save_valid(pb, n, kk, t0, t1);
+      sv = save_at(pb, n, kk);
+      if constexpr (DF) split_df(sv, svh, svl);
+    }
   }
 
   // Hairer, Norsett & Wanner I, Sec. II.4 starting step (FP64 norms).
@@ -172,7 +212,7 @@ struct Traj {
   __device__ void init(const Problem& pb, long long traj) {
     n = traj;
     status = 0; nacc = 0; nrej = 0; kk = 0;
-    done = false; failed = false; rec_ok = true; chunk = -1;
+    done = false; failed = false; rec_ok = true; chunk = -1; sv_ok = false;
     t0 = pb.t0[n];
     t1 = pb.t1[n];
     bool fin = isfinite(t0) && isfinite(t1);
@@ -225,6 +265,7 @@ struct Traj {
       }
       kk++;
     }
+    load_sv(pb);
     Sys::f(stage_time(t0), y, p, k1);
     t = t0;
     tc = 0.0;
@@ -233,6 +274,11 @@ struct Traj {
     atolf = float(pb.atol);
     rtolf = float(pb.rtol);
     h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step(pb);
+    if constexpr (DF) {
+      split_df(t0, th, tl);
+      split_df(t1, t1h, t1l);
+      hf = float(h);
+    }
   }
 
   // Stages of one step of length hh from (tt, y): Eq. rk. k[0] = k1 on entry.
@@ -255,17 +301,18 @@ struct Traj {
           else Yj[i] = y[i] + hh * acc;
           if (Y) Y[j][i] = Yj[i];
         }
-        Sys::f(stage_time(tt + Tab::c(j) * hh), Yj, p, k[j]);
+        if constexpr (DF) Sys::f(R(tt) + R(Tab::c(j)) * hr, Yj, p, k[j]);
+        else Sys::f(stage_time(tt + Tab::c(j) * hh), Yj, p, k[j]);
       }
     }
   }
 
   // Solution at tt + sig*hh inside the accepted step just taken (Eq. dense; Verner 7: shortened
   // step from the start of the step). k holds the step's stages.
-  __device__ void dense_point(double tt, double hh, double sig, R (*k)[D], R* hi, R* lo) const {
+  __device__ void dense_point(double tt, double hh, R sig, R (*k)[D], R* hi, R* lo) const {
     if constexpr (Tab::DENSE_POLY) {
       R w[S];
-      Tab::dense(R(sig), w);
+      Tab::dense(sig, w);
       const R hr = R(hh);
 #pragma unroll
       for (int i = 0; i < D; i++) {
@@ -277,7 +324,7 @@ struct Traj {
       }
     } else {
       R ks[S][D];
-      const double hs = sig * hh;
+      const double hs = double(sig) * hh;
       stages(tt, hs, ks, nullptr, Tab::NREV);
       const R hr = R(hs);
 #pragma unroll
@@ -292,7 +339,7 @@ struct Traj {
     }
   }
 
-  __device__ void record_slot(const Problem& pb, bool last) {
+  __device__ void record_slot(const Problem& pb, bool last, R hstep) {
     const int a = nacc - 1;  // index of the step just accepted
     if (!rec_ok) return;
     const int o = a % kChunk;
@@ -306,16 +353,30 @@ struct Traj {
     unsigned char* slot = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader +
                           (long long)o * kSlotBytes;
     if constexpr (F32) {
-      float* f = reinterpret_cast<float*>(slot);
+      // 16-byte stores: slots start 16-byte aligned (16-byte header, 8 D + 32 bytes per slot)
+      float v[2 * D];
 #pragma unroll
-      for (int i = 0; i < D; i++) { f[i] = y[i]; f[D + i] = ylo[i]; }
+      for (int i = 0; i < D; i++) { v[i] = y[i]; v[D + i] = ylo[i]; }
+      if constexpr ((2 * D) % 4 == 0) {
+        float4* f4 = reinterpret_cast<float4*>(slot);
+#pragma unroll
+        for (int q = 0; q < (2 * D) / 4; q++) f4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      } else {
+        float2* f2 = reinterpret_cast<float2*>(slot);
+#pragma unroll
+        for (int q = 0; q < D; q++) f2[q] = make_float2(v[2 * q], v[2 * q + 1]);
+      }
     } else {
       double* f = reinterpret_cast<double*>(slot);
 #pragma unroll
       for (int i = 0; i < D; i++) f[i] = y[i];
     }
-    double* tail = reinterpret_cast<double*>(slot + 8 * D);
-    tail[0] = t; tail[1] = tc; tail[2] = h; tail[3] = last ? 1.0 : 0.0;
+    if constexpr (DF) {
+      *reinterpret_cast<float4*>(slot + kTailOff) = make_float4(th, tl, hstep, last ? 1.0f : 0.0f);
+    } else {
+      double* tail = reinterpret_cast<double*>(slot + kTailOff);
+      tail[0] = t; tail[1] = tc; tail[2] = h; tail[3] = last ? 1.0 : 0.0;
+    }
   }
 
   __device__ void fail(int32_t bit) {
@@ -324,30 +385,63 @@ struct Traj {
     done = true;
   }
 
+  // the interval closed without a clipped last step: the remaining outputs are the state
+  __device__ void close_interval(const Problem& pb) {
+    while (kk < pb.K) {
+      if (save_valid(pb, n, kk, t0, t1)) write_out(pb, kk, y, ylo);
+      kk++;
+    }
+    done = true;
+  }
+
+  // safety * ||e||^-beta1 * err_prev^beta2 clamped to [alpha_min, alpha_max] (Eq. controller).
+  // The FP32 modes take the power in FP32 from log2 ||e|| (||e|| = 0 gives alpha_max, inf alpha_min).
+  __device__ __forceinline__ float factor_f(const Problem& pb, float lerr) const {
+    float lf = -pb.fbeta1 * lerr;
+    if (pb.fbeta2 != 0.0f) lf += pb.fbeta2 * lerr_prev;
+    const float fac = pb.fsafety * exp2f(lf);
+    return fminf(fmaxf(fac, pb.falpha_min), pb.falpha_max);
+  }
+  __device__ __forceinline__ double factor_d(const Problem& pb, double err) const {
+    double fac = pb.safety * pow(err, -pb.beta1) * (pb.beta2 != 0.0 ? pow(err_prev, pb.beta2) : 1.0);
+    if (fac > pb.alpha_max) fac = pb.alpha_max;
+    if (fac < pb.alpha_min) fac = pb.alpha_min;
+    return fac;
+  }
+
   // One step attempt.
   __device__ void attempt(const Problem& pb) {
-    const double rem = (t1 - t) + tc;
-    if (rem <= 0.0) {  // the interval closed without a final step: remaining outputs are y
-      while (kk < pb.K) {
-        if (save_valid(pb, n, kk, t0, t1)) write_out(pb, kk, y, ylo);
-        kk++;
-      }
-      done = true;
-      return;
-    }
-    if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+    // ---- step length: land exactly on t1, or stop on underflow / too many attempts
     bool last = false;
-    if (h * (1.0 + 4.0 * DBL_EPSILON) >= rem) {
-      h = rem;
-      last = true;
+    R hr;
+    if constexpr (DF) {
+      const float rem = (t1h - th) + (t1l - tl);
+      if (!(rem > 0.0f)) { close_interval(pb); return; }
+      if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+      if (hf * (1.0f + 4.0f * FLT_EPSILON) >= rem) {
+        hf = rem;
+        last = true;
+      } else {
+        const float tm = fmaxf(fabsf(th), fabsf(t1h));
+        if (!(hf >= 16.0f * kEps48 * tm)) { fail(isnan(hf) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW); return; }
+      }
+      hr = hf;
     } else {
-      const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
-      if (!(h >= 16.0 * DBL_EPSILON * tm)) { fail(isnan(h) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW); return; }
+      const double rem = (t1 - t) + tc;
+      if (rem <= 0.0) { close_interval(pb); return; }
+      if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+      if (h * (1.0 + 4.0 * DBL_EPSILON) >= rem) {
+        h = rem;
+        last = true;
+      } else {
+        const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
+        if (!(h >= 16.0 * DBL_EPSILON * tm)) { fail(isnan(h) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW); return; }
+      }
+      hr = R(h);
     }
+    // ---- stages 2..S (the last one is the new state for FSAL pairs), Eq. rk
     R k[S][D];
     R Ylast[D];
-    const R hr = R(h);
-    // stages 2..S (the last one is the new state for FSAL pairs)
 #pragma unroll
     for (int i = 0; i < D; i++) k[0][i] = k1[i];
 #pragma unroll
@@ -363,9 +457,10 @@ struct Traj {
         else Yj[i] = y[i] + h * acc;
         if (j == S - 1) Ylast[i] = Yj[i];
       }
-      Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
+      if constexpr (DF) Sys::f((th + tl) + R(Tab::c(j)) * hr, Yj, p, k[j]);
+      else Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
     }
-    // new state: increments h sum b_j k_j
+    // ---- new state: y + h sum b_j k_j
     R ynew[D], ynlo[DL];
 #pragma unroll
     for (int i = 0; i < D; i++) {
@@ -383,62 +478,82 @@ struct Traj {
         }
       }
     }
-    // error estimate e = h sum (b_j - bhat_j) k_j and its scaled RMS norm, Eq. errnorm:
-    // ||e|| = sqrt(sq / d), sq = sum_i (e_i / s_i)^2 accumulated in FP64 in both precisions
-    double sq = 0.0;
+    // ---- error estimate e = h sum (b_j - bhat_j) k_j and its scaled RMS norm, Eq. errnorm:
+    // ||e|| = sqrt(sq / d), sq = sum_i (e_i / s_i)^2, s_i = atol + rtol max(|y_i|, |y+_i|)
+    bool accept, bad;
+    double err = 0.0;
+    float lerr = 0.0f;
+    if constexpr (PM == 0) {
+      double sq = 0.0;
 #pragma unroll
-    for (int i = 0; i < D; i++) {
-      R acc = R(0);
+      for (int i = 0; i < D; i++) {
+        double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < S; j++)
-        if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * k[j][i];
-      if constexpr (F32) {
-        const R e = hr * acc;
-        const R a = fabsf(y[i]), b = fabsf(ynew[i]);
-        const R sc = atolf + rtolf * (a > b ? a : b);
-        const double r = double(__fdividef(e, sc));
-        sq += r * r;
-      } else {
+        for (int j = 0; j < S; j++)
+          if (Tab::bt(j) != 0.0) acc = acc + Tab::bt(j) * k[j][i];
         const double e = h * acc;
         const double a = fabs(y[i]), b = fabs(ynew[i]);
         const double sc = pb.atol + pb.rtol * (a > b ? a : b);
         const double r = e / sc;
         sq += r * r;
       }
-    }
-    // accept iff ||e|| <= 1; new step h * clamp(safety ||e||^-beta1 err_prev^beta2, alpha_min,
-    // alpha_max) after accepted and rejected attempts alike (Eq. controller; PI form for beta2 != 0)
-    bool accept;
-    double err = 0.0;
-    float lerr = 0.0f;
-    if constexpr (F32) {
-      accept = sq <= double(D);
-      lerr = 0.5f * (__log2f(float(sq)) - log2f(float(D)));  // log2 ||e||
-    } else {
       err = sqrt(sq / D);
       accept = err <= 1.0;
+      bad = isnan(err);
+    } else {
+      // PM 1 accumulates the squares in FP64, PM 2 in FP32
+      using Acc = typename std::conditional<PM == 1, double, float>::type;
+      Acc sq = Acc(0);
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        R acc = R(0);
+#pragma unroll
+        for (int j = 0; j < S; j++)
+          if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * k[j][i];
+        const R e = hr * acc;
+        const R a = fabsf(y[i]), b = fabsf(ynew[i]);
+        const R sc = atolf + rtolf * (a > b ? a : b);
+        const Acc r = Acc(__fdividef(e, sc));
+        sq += r * r;
+      }
+      accept = sq <= Acc(D);
+      lerr = 0.5f * (__log2f(float(sq)) - log2f(float(D)));  // log2 ||e||
+      bad = isnan(sq);
     }
     if (accept) {
       nacc += 1;
-      if (pb.record) record_slot(pb, last);
-      // outputs inside (t, t + h]
+      if (pb.record) record_slot(pb, last, hr);
+      // ---- outputs inside (t, t + h] (Eq. dense), or the new state itself at t1
       while (kk < pb.K) {
-        if (!save_valid(pb, n, kk, t0, t1)) { kk++; continue; }
-        const double sv = save_at(pb, n, kk);
-        const double dk = (sv - t) + tc;
-        if (last && sv == t1) {
+        if (!sv_ok) { kk++; load_sv(pb); continue; }
+        bool at_end, inside;
+        R sig;
+        if constexpr (DF) {
+          at_end = last && svh == t1h && svl == t1l;
+          const float dk = (svh - th) + (svl - tl);
+          inside = last || dk <= hf;
+          sig = fminf(fmaxf(__fdividef(dk, hf), 0.0f), 1.0f);
+        } else {
+          at_end = last && sv == t1;
+          const double dk = (sv - t) + tc;
+          inside = last || dk <= h;
+          double sg = dk / h;
+          if (sg > 1.0) sg = 1.0;
+          if (sg < 0.0) sg = 0.0;
+          sig = R(sg);
+        }
+        if (at_end) {
           write_out(pb, kk, ynew, F32 ? ynlo : ynew);
-        } else if (last || dk <= h) {
-          double sig = dk / h;
-          if (sig > 1.0) sig = 1.0;
-          if (sig < 0.0) sig = 0.0;
+        } else if (inside) {
           R hi[D], lo[D];
-          dense_point(t, h, sig, k, hi, lo);
+          if constexpr (DF) dense_point(double(th) + double(tl), double(hf), sig, k, hi, lo);
+          else dense_point(t, h, sig, k, hi, lo);
           write_out(pb, kk, hi, lo);
         } else {
           break;
         }
         kk++;
+        load_sv(pb);
       }
 #pragma unroll
       for (int i = 0; i < D; i++) {
@@ -447,40 +562,39 @@ struct Traj {
         if constexpr (Tab::FSAL) k1[i] = k[S - 1][i];
       }
       if (last) {
-        t = t1; tc = 0.0; done = true;
+        done = true;
+        if constexpr (DF) { th = t1h; tl = t1l; }
+        else { t = t1; tc = 0.0; }
+      } else if constexpr (DF) {
+        float s, e2;  // (th, tl) += hf without rounding error
+        two_sum(th, hf, s, e2);
+        const float l = tl + e2;
+        th = s + l;
+        tl = l - (th - s);
+        if constexpr (!Tab::FSAL) Sys::f(th + tl, y, p, k1);
+        hf = hf * factor_f(pb, lerr);
+        lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;  // log2(1e-4)
       } else {
         const double yk = h - tc;  // Kahan summation of the time
         const double tn = t + yk;
         tc = (tn - t) - yk;
         t = tn;
         if constexpr (!Tab::FSAL) Sys::f(stage_time(t), y, p, k1);
-        h = h * factor(pb, err, lerr);
-        if constexpr (F32) lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;  // log2(1e-4)
-        else err_prev = err > 1e-4 ? err : 1e-4;
+        if constexpr (F32) {
+          h = h * double(factor_f(pb, lerr));
+          lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;
+        } else {
+          h = h * factor_d(pb, err);
+          err_prev = err > 1e-4 ? err : 1e-4;
+        }
       }
     } else {
       nrej += 1;
-      const bool bad = F32 ? isnan(sq) : isnan(err);
-      h = h * (bad ? pb.alpha_min : factor(pb, err, lerr));
+      if constexpr (DF) hf = hf * (bad ? pb.falpha_min : factor_f(pb, lerr));
+      else if constexpr (F32) h = h * (bad ? pb.alpha_min : double(factor_f(pb, lerr)));
+      else h = h * (bad ? pb.alpha_min : factor_d(pb, err));
       err_prev = 1.0;
       lerr_prev = 0.0f;
-    }
-  }
-
-  // safety * ||e||^-beta1 * err_prev^beta2 clamped to [alpha_min, alpha_max]. F32: the power is
-  // taken in FP32 from log2 ||e|| (err = 0 gives alpha_max, err = inf gives alpha_min).
-  __device__ __forceinline__ double factor(const Problem& pb, double err, float lerr) const {
-    if constexpr (F32) {
-      float lf = -float(pb.beta1) * lerr;
-      if (pb.beta2 != 0.0) lf += float(pb.beta2) * lerr_prev;
-      float fac = float(pb.safety) * exp2f(lf);
-      fac = fminf(fmaxf(fac, float(pb.alpha_min)), float(pb.alpha_max));
-      return double(fac);
-    } else {
-      double fac = pb.safety * pow(err, -pb.beta1) * (pb.beta2 != 0.0 ? pow(err_prev, pb.beta2) : 1.0);
-      if (fac > pb.alpha_max) fac = pb.alpha_max;
-      if (fac < pb.alpha_min) fac = pb.alpha_min;
-      return fac;
     }
   }
 

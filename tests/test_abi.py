@@ -71,5 +71,10 @@ def test_workspace_sizes(lib):
     small = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 0, 0.0)
     big = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 1, 500.0)
     assert small >= 256 and big > small
-    # a tape chunk holds 32 slots of (8 d + 32) bytes behind a 16-byte header
-    assert (big - small) == (1000 * (16 + 1) + 1) * (16 + 32 * (8 * 6 + 32))
+    # a tape chunk holds 32 slots of (8 d rounded up to 16, + 32) bytes behind a 16-byte header
+    assert (big - small) == (1000 * (16 + 1) + 1) * (16 + 32 * (48 + 32))
+    for sysid, d in ((2, 9), (3, 3)):
+        a = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 0, 0.0)
+        b = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 1, 500.0)
+        slot = (8 * d + 15) // 16 * 16 + 32
+        assert slot % 16 == 0 and (b - a) == (1000 * (16 + 1) + 1) * (16 + 32 * slot)

@@ -35,7 +35,7 @@ STATES = {
 
 
 @pytest.mark.parametrize("system", list(STATES))
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5), ("fp32df", 2e-5)])
 def test_vjp_dot_product(system, precision, tol):
     ensure_built()
     rng = np.random.default_rng(5)
@@ -100,15 +100,16 @@ def _gerr(g, ref):
     return np.linalg.norm(gy - ry, axis=1) / np.linalg.norm(ry, axis=1)
 
 
-@pytest.mark.parametrize("kernel", ["plain", "persistent"])
-def test_adjoint_fp32_close_to_fp64_adjoint(kernel):
-    """Precision alone: FP32-stage and FP64 adjoints at the same tolerance on 3 Gyr orbits."""
-    e = W.mw(n=512, seed=49, rtol=3.16e-8)
+@pytest.mark.parametrize("kernel,prec", [("plain", "fp32"), ("persistent", "fp32"), ("persistent", "fp32df")])
+def test_adjoint_fp32_meets_gradient_budget(kernel, prec):
+    """FP32-stage adjoint on 3 Gyr orbits at a tolerance meeting the gradient budget (1e-3, Sec. 3)
+    against the oracle's converged forward-sensitivity gradient."""
+    e = W.mw(n=256, seed=49, rtol=3.16e-9)
     w = np.random.default_rng(2).normal(size=(e.n, 1, 6))
-    a = gpu_vjp(e, w, precision="fp32", kernel=kernel)
-    b = gpu_vjp(e, w, precision="fp64", kernel=kernel)
+    ref = O.grad("mw", e.y0, e.params, e.t0, e.t1, e.saveat, w, rtol=1e-11, atol=1e-11, method="vern7")
+    a = gpu_vjp(e, w, precision=prec, kernel=kernel)
     assert np.all(a["status"] == 0)
-    assert np.percentile(_gerr(a, b), 99) <= 1e-3, np.percentile(_gerr(a, b), 99)
+    assert np.percentile(_gerr(a, ref), 99) <= 1e-3, np.percentile(_gerr(a, ref), 99)
 
 
 def test_adjoint_converges_to_oracle_gradient():
@@ -160,7 +161,7 @@ def test_reuse_tape_matches_rerun():
     ws = api.Workspace(dev)
     y0 = torch.as_tensor(e.y0, device=dev)
     w = torch.as_tensor(np.random.default_rng(4).normal(size=(e.n, 1, 6)), device=dev)
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp32", "fp32df"):
         s = api.solve("mw", y0, e.params, e.t0, e.t1, e.saveat, e.rtol, e.atol, precision=prec, record_tape=True,
                       workspace=ws, steps_hint=2000)
         a = api.vjp("mw", y0, e.params, e.t0, e.t1, e.saveat, e.rtol, e.atol, w, precision=prec, reuse_tape=s,
@@ -180,6 +181,6 @@ def test_autograd_function():
     y, st = api.solve_autograd("mw", y0, pr, e.t0, e.t1, e.saveat, e.rtol, e.atol)
     loss = 0.5 * (y ** 2).sum()
     loss.backward()
-    g = gpu_vjp(e, y.detach().cpu().numpy())
-    assert np.allclose(y0.grad.cpu().numpy(), g["dLdy0"], rtol=0, atol=0)
-    assert np.allclose(pr.grad.cpu().numpy(), g["dLdparams"], rtol=0, atol=0)
+    g = gpu_vjp(e, y.detach().cpu().numpy(), kernel="persistent")
+    assert np.array_equal(y0.grad.cpu().numpy(), g["dLdy0"])
+    assert np.array_equal(pr.grad.cpu().numpy(), g["dLdparams"])

@@ -69,13 +69,37 @@ def test_fp64_same_algorithm_parity(system, gen, method, kernel):
     assert np.array_equal(g["y"][empty], ref["y"][empty])
 
 
-def test_persistent_kernel_is_bitwise_equal_to_plain():
-    for prec in ("fp64", "fp32"):
-        e = W.mw(n=3000, seed=31, t1=1000.0)
+def test_persistent_kernel_matches_plain():
+    """Same per-trajectory algorithm in both kernels. FP64: the compiler may fuse multiply-adds
+    differently in the two, so results agree to rounding and step counts almost always. FP32 modes:
+    the FP32 rounding noise of the error estimate is a sizeable fraction of the tolerance, so the
+    two codegens flip borderline accept tests and the step sequences diverge; the results then agree
+    to the tolerance level, judged in the orbit error measure (Eq. st-fwderr) against the budget."""
+    e = W.mw(n=3000, seed=31, t1=1000.0)
+    a = gpu_solve(e, precision="fp64", kernel="plain")
+    b = gpu_solve(e, precision="fp64", kernel="persistent")
+    assert np.array_equal(a["status"], b["status"])
+    same = (a["n_accept"] == b["n_accept"]) & (a["n_reject"] == b["n_reject"])
+    assert same.mean() > 0.95, same.mean()
+    assert rel_err(a["y"], b["y"])[same].max() <= 1e-10
+    rE, vE = M.orbit_scales("mw", e.y0, e.params)
+    for prec in ("fp32", "fp32df"):
         a = gpu_solve(e, precision=prec, kernel="plain")
         b = gpu_solve(e, precision=prec, kernel="persistent")
-        for k in ("y", "status", "n_accept", "n_reject"):
-            assert np.array_equal(a[k], b[k]), (prec, k)
+        assert np.array_equal(a["status"], b["status"])
+        err = M.orbit_error(a["y"][:, -1], b["y"][:, -1], rE, vE)
+        assert M.p99(err) <= 1e-4, (prec, M.p99(err))
+        assert abs(a["n_accept"].mean() / b["n_accept"].mean() - 1) < 0.02
+
+
+def test_repeated_launches_are_bitwise_reproducible():
+    for prec in ("fp64", "fp32", "fp32df"):
+        for kernel in ("plain", "persistent"):
+            e = W.mw(n=2000, seed=38, t1=800.0)
+            a = gpu_solve(e, precision=prec, kernel=kernel)
+            b = gpu_solve(e, precision=prec, kernel=kernel)
+            for k in ("y", "status", "n_accept", "n_reject"):
+                assert np.array_equal(a[k], b[k]), (prec, kernel, k)
 
 
 def _converged(e, method="vern7"):
@@ -90,32 +114,44 @@ def test_mw_meets_orbit_budget_at_searched_tolerance(kernel):
     e = W.mw(n=1024, seed=32)
     ref = _converged(e)
     rE, vE = M.orbit_scales("mw", e.y0, e.params)
-    for prec, rtol in (("fp32", 1.78e-8), ("fp64", 3.16e-8)):
+    for prec, rtol in (("fp32", 1.78e-8), ("fp32df", 1.78e-8), ("fp64", 3.16e-8)):
         g = gpu_solve(e, precision=prec, kernel=kernel, rtol=rtol, atol=rtol)
         assert np.all(g["status"] == 0)
         err = M.orbit_error(g["y"][:, -1], ref["y"][:, -1], rE, vE)
         assert M.accepted(err, 1e-4), (prec, M.p99(err), err.max())
 
 
-def test_fp32_stages_close_to_fp64_at_same_tolerance():
-    """The FP32-stage solve differs from the FP64 solve of the same tolerance by much less than the
+@pytest.mark.parametrize("prec", ["fp32", "fp32df"])
+def test_fp32_modes_close_to_fp64_at_same_tolerance(prec):
+    """An FP32-stage solve differs from the FP64 solve of the same tolerance by much less than the
     budget: precision adds at most a small fraction to the truncation error."""
     e = W.mw(n=2048, seed=37)
     rE, vE = M.orbit_scales("mw", e.y0, e.params)
-    a = gpu_solve(e, precision="fp32", kernel="persistent", rtol=3.16e-8, atol=3.16e-8)
+    a = gpu_solve(e, precision=prec, kernel="persistent", rtol=3.16e-8, atol=3.16e-8)
     b = gpu_solve(e, precision="fp64", kernel="persistent", rtol=3.16e-8, atol=3.16e-8)
     err = M.orbit_error(a["y"][:, -1], b["y"][:, -1], rE, vE)
     assert M.p99(err) <= 1e-4, M.p99(err)
 
 
+def test_fp32df_dense_outputs_and_time_pair():
+    """FP32-pair time: outputs at 11 times over 100 time units (isochrone) stay within the FP32 stage
+    accuracy of the FP64 oracle, and the output at t1 comes from the clipped last step."""
+    e = W.isochrone(n=512, seed=39)
+    ref = oracle_solve(e, rtol=1e-12, atol=1e-12, method="vern7")
+    g = gpu_solve(e, precision="fp32df", kernel="persistent", rtol=1e-8, atol=1e-8)
+    assert np.all(g["status"] == 0)
+    assert rel_err(g["y"], ref["y"]).max() <= 2e-4
+    assert np.array_equal(g["y"][:, 0], e.y0)
+
+
 def test_quintessence_fp32_stages_meet_distance_budget():
     e = W.quintessence(n=1024, seed=33, rtol=1e-6)
     ref = _converged(e, method="tsit5")
-    for method in ("tsit5", "dopri5"):
-        g = gpu_solve(e, method=method, precision="fp32")
+    for method, prec in (("tsit5", "fp32"), ("dopri5", "fp32"), ("tsit5", "fp32df"), ("dopri5", "fp32df")):
+        g = gpu_solve(e, method=method, precision=prec)
         assert np.all(g["status"] == 0)
         err = M.distance_error(g["y"], ref["y"], e.params, e.saveat)
-        assert M.accepted(err, 1e-4), (method, M.p99(err))
+        assert M.accepted(err, 1e-4), (method, prec, M.p99(err))
 
 
 def test_precession_fp64_meets_angle_budget():
