@@ -139,6 +139,26 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
            double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* workspace,
            size_t workspace_bytes, void* cuda_stream);
 
+/* Size of the built-in scratch array of gs_vjp_noalloc (64 MiB). */
+#define GS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* gs_vjp for callers that cannot allocate device memory or pass a workspace (code inside another
+ * framework's memory pool, plug-ins whose host owns all device allocations, loops where an
+ * allocation could stall). The paper has no counterpart. Same arguments and results as gs_vjp
+ * without the workspace; opt->reuse_tape must be 0 (the forward solve is always re-run).
+ * The scratch (work counters and step tape) is a GS_NOALLOC_SCRATCH_BYTES array inside the library,
+ * present on every GPU that loads it until the process exits; nothing is allocated or freed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and caches
+ * it: make that first call before any stream capture. Calls share the array and it keeps the last
+ * call's contents (the call clears what must start at zero); calls that overlap on the GPU race, so
+ * issue them one after another. N whose per-trajectory bookkeeping (8 N bytes, padded, plus a 256-byte
+ * header and one tape chunk) exceeds the array is rejected with GS_ERR_WORKSPACE; trajectories whose
+ * steps do not fit in the rest of the array get GS_ST_TAPE_OVERFLOW and NaN gradients. */
+int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+                   const double* t1, double rtol, double atol, int32_t K, const double* saveat,
+                   const gs_options* opt, const double* dLdy, double* dLdy0, double* dLdparams,
+                   double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* cuda_stream);
+
 /* Workspace bytes for N trajectories. for_vjp = 0: the persistent kernel's counter only.
  * for_vjp != 0: room for a step tape of `steps_hint` accepted steps per trajectory on average
  * (rounded up to whole chunks per trajectory), plus the chunk table sized by

@@ -161,6 +161,11 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 }  // namespace
 
+namespace gs {
+// error reporting for entry points defined in other translation units
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace gs
+
 extern "C" {
 
 void gs_default_options(gs_options* o) {
