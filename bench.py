@@ -401,6 +401,146 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_workload(args):
+    """Other workloads (one JSON line each, not the headline): per variant the forward solves/s and,
+    where the workload asks for gradients, forward+adjoint solves/s, with the error against a
+    converged FP64 Verner 7 solve of a sample and the budget test (Eq. accept)."""
+    import torch
+
+    from paper_2609_28458_gb300 import api
+    from paper_2609_28458_gb300 import build as gsbuild
+    from paper_2609_28458_gb300 import metrics as M
+    from paper_2609_28458_gb300 import workloads as W
+
+    gsbuild.build()
+    dev = torch.device("cuda")
+    name = args.workload
+    if name == "isochrone":
+        e = W.isochrone(n=4096, seed=0)
+        rows = [("fp64", "plain", "tsit5", 1e-10, 1e-12, False), ("fp64", "persistent", "tsit5", 1e-10, 1e-12, False),
+                ("fp64", "persistent", "tsit5", 1e-10, 1e-12, True)]
+        budget, meas = 1e-4, "orbit"
+    elif name in ("precession", "precession_paper"):
+        # "precession": from the 20 Hz gravitational-wave frequency to v = 0.3; "precession_paper": the
+        # paper's own interval r = 100 M -> 10 M (Sec. 5)
+        e = W.precession(n=1_000_000, seed=2000, paper_interval=(name == "precession_paper"))
+        rows = [("fp64", "plain", "vern7", 3.16e-9, 3.16e-9, True), ("fp64", "persistent", "vern7", 3.16e-9, 3.16e-9, True),
+                ("fp64", "plain", "tsit5", 5.62e-10, 5.62e-10, False),
+                ("fp64", "persistent", "tsit5", 5.62e-10, 5.62e-10, False)]
+        budget, meas = 2e-7, "angle"
+    elif name == "quintessence":
+        e = W.quintessence(n=10_000, seed=3000)
+        rows = [(prec, kern, m, r, 1e-3 * r, True) for r in (1e-4, 1e-5, 1e-6) for m in ("dopri5", "tsit5")
+                for prec, kern in (("fp32df", "persistent"),)] + [("fp64", "plain", "tsit5", 1e-6, 1e-9, True)]
+        budget, meas = 1e-4, "distance"
+    else:  # loghalo: the paper's stream system, rtol = atol = 3.16e-7 (Sec. 3)
+        e = W.loghalo(n=1_000_000, seed=4000)
+        rows = [("fp64", "plain", "tsit5", 3.16e-7, 3.16e-7, True), ("fp64", "persistent", "tsit5", 3.16e-7, 3.16e-7, True),
+                ("fp32df", "persistent", "tsit5", 3.16e-7, 3.16e-7, True)]
+        budget, meas = 1e-4, "orbit"
+    d, p = e.y0.shape[1], e.params.shape[1]
+    y0 = torch.as_tensor(e.y0, device=dev)
+    pr = torch.as_tensor(e.params, device=dev) if p else None
+    t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
+    ns = min(e.n, 16384)
+    idx_np = np.sort(np.random.default_rng(5).choice(e.n, ns, replace=False))
+    idx = torch.as_tensor(idx_np, device=dev)
+    svs = sv[idx] if sv.dim() == 2 else sv
+    ratm = 1e-14 if name == "quintessence" else 1e-12
+    system = "precession" if name.startswith("precession") else name
+    ref = api.solve(system, y0[idx], pr[idx] if p else None, t0[idx], t1[idx], svs, 1e-12, ratm, method="vern7",
+                    precision="fp64", max_steps=2_000_000)["y"].cpu().numpy()
+    if meas == "orbit":
+        rE, vE = M.orbit_scales(system, e.y0[idx_np], e.params[idx_np] if p else None)
+
+    def err_of(y):
+        y = y[idx].cpu().numpy()
+        if meas == "orbit":
+            return M.orbit_error(y, ref, rE, vE)
+        if meas == "angle":
+            ok = (e.t1[idx_np] > e.t0[idx_np])
+            er = M.precession_error(y[:, -1], ref[:, -1])
+            return er[ok]
+        return M.distance_error(y, ref, e.params[idx_np], e.saveat)
+
+    def timeit(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    out = []
+    for prec, kern, meth, rtol, atol, grad in rows:
+        kw = dict(method=meth, precision=prec, kernel=kern, max_steps=2_000_000)
+        s = api.solve(system, y0, pr, t0, t1, sv, rtol, atol, **kw)
+        f_ms = timeit(lambda: api.solve(system, y0, pr, t0, t1, sv, rtol, atol, **kw))
+        er = err_of(s["y"])
+        row = {"precision": prec, "kernel": kern, "method": meth, "rtol": rtol, "atol": atol, "fwd_ms": f_ms,
+               "fwd_solves_per_s": e.n / (f_ms / 1e3), "us_per_solve": 1e3 * f_ms / e.n, "p99_err": M.p99(er),
+               "max_err": float(np.max(er)), "accepted": M.accepted(er, budget),
+               "attempts_mean": float((s["n_accept"] + s["n_reject"]).double().mean())}
+        if grad:
+            ws = api.Workspace(dev)
+            nb = api.tape_bytes(system, e.n, n_accept=s["n_accept"])
+            w = torch.ones_like(s["y"])
+
+            def fg():
+                ss = api.solve(system, y0, pr, t0, t1, sv, rtol, atol, record_tape=True, workspace=ws, tape_nbytes=nb, **kw)
+                api.vjp(system, y0, pr, t0, t1, sv, rtol, atol, w, reuse_tape=ss, workspace=ws, **kw)
+
+            g_ms = timeit(fg)
+            row.update(fwd_grad_ms=g_ms, fwd_grad_solves_per_s=e.n / (g_ms / 1e3))
+            del ws
+        if name in ("isochrone", "quintessence") and kern == "persistent":
+            gsg = api.GraphedStep(system, y0, pr, t0, t1, sv, rtol, atol, grad=grad, **kw)
+            row["graph_replay_ms"] = timeit(gsg.replay)
+            del gsg
+        out.append(row)
+        torch.cuda.empty_cache()
+        log(json.dumps(row))
+    print(json.dumps({"metric": METRIC, "workload": name, "n": e.n, "budget": budget, "error_measure": meas,
+                      "reference": "FP64 Verner 7 at rtol 1e-12 on a %d-member sample" % ns, "rows": out}), flush=True)
+
+
+def run_case(args):
+    """Small profiling cases of the headline kernels (no JSON line): the seeded MW workload with
+    --n orbits at --rtol, solved twice. 'fwd': persistent forward without a tape; 'fwdrev': forward
+    recording its tape, then the persistent reverse sweep."""
+    import torch
+
+    from paper_2609_28458_gb300 import api
+    from paper_2609_28458_gb300 import build as gsbuild
+    from paper_2609_28458_gb300 import workloads as W
+
+    gsbuild.build()
+    dev = torch.device("cuda")
+    e = W.mw(n=args.n, seed=1000)
+    y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
+    t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
+    kw = dict(precision=args.precision, kernel="persistent")
+    if args.case == "fwd":
+        for _ in range(2):
+            s = api.solve("mw", y0, pr, t0, t1, sv, args.rtol, args.rtol, **kw)
+    else:
+        ws = api.Workspace(dev)
+        probe = api.solve("mw", y0, pr, t0, t1, sv, args.rtol, args.rtol, **kw)
+        nb = api.tape_bytes("mw", args.n, n_accept=probe["n_accept"])
+        for _ in range(2):
+            s = api.solve("mw", y0, pr, t0, t1, sv, args.rtol, args.rtol, record_tape=True, workspace=ws,
+                          tape_nbytes=nb, **kw)
+            api.vjp("mw", y0, pr, t0, t1, sv, args.rtol, args.rtol, s["y"] - 0.0, reuse_tape=s, workspace=ws, **kw)
+    torch.cuda.synchronize()
+    log("case %s: n=%d failed=%d mean accepted steps %.1f" % (args.case, args.n, int((s["status"] != 0).sum()),
+                                                              float(s["n_accept"].double().mean())))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,8 +551,17 @@ def main():
     ap.add_argument("--acc-sample", type=int, default=16384)
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--case", choices=["fwd", "fwdrev"], help="run a small profiling case instead")
+    ap.add_argument("--workload", default="mw",
+                    choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "loghalo"])
+    ap.add_argument("--precision", default="fp32df")
+    ap.add_argument("--rtol", type=float, default=1e-8)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.workload != "mw":
+        run_workload(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

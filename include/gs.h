@@ -167,6 +167,21 @@ int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* pa
 size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
                           double steps_hint);
 
+/* Forward sensitivities (Sec. 2.3, Eq. sens; Appendix A, Eq. stage-sens): the solve of gs_solve carrying
+ * m tangent directions, S = dy/d(direction), integrated with the same Runge-Kutta steps as y (step
+ * control on y alone), so S is the exact derivative of the numerical solution on those steps.
+ *  dy0 [N,d,m]: S(t0), the direction of the initial state (NULL = 0).
+ *  dparams [N,p,m]: the parameter direction (NULL = 0); e.g. unit vectors give dy/dtheta_q.
+ *  y_out [N,K,d] as gs_solve; S_out [N,K,d,m]: the sensitivities at the output times.
+ *  Precision GS_FP64 or GS_FP32_DF; persistent kernel; the workspace holds its work counter
+ *  (gs_workspace_bytes(..., for_vjp = 0, ...)). Directions are processed up to 4 per launch
+ *  (1 for GS_VERN7), so m > 4 repeats the solve per group. */
+int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+           const double* t1, double rtol, double atol, int32_t K, const double* saveat,
+           const gs_options* opt, int32_t m, const double* dy0, const double* dparams, double* y_out,
+           double* S_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* workspace,
+           size_t workspace_bytes, void* cuda_stream);
+
 /* Evaluate f (Eq. ivp) and its vector-Jacobian products for M states, as the solver does:
  *  f [M,d] = f(t, y, theta);  gy [M,d] = J_y^T w;  gp [M,p] = J_theta^T w  (gy, gp may be NULL).
  *  precision selects the FP64 (GS_FP64) or FP32 (the two FP32 modes) instantiation. */

@@ -19,8 +19,8 @@ ST_MAX_STEPS, ST_H_UNDERFLOW, ST_NONFINITE, ST_EMPTY_INTERVAL, ST_SAVEAT_OUTSIDE
 ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_WORKSPACE = 0, 1, 2, 3
 
-EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_vjp_noalloc", "gs_workspace_bytes", "gs_rhs",
-           "gs_last_error", "gs_version")
+EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_jvp", "gs_vjp_noalloc", "gs_workspace_bytes",
+           "gs_rhs", "gs_last_error", "gs_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -65,6 +65,10 @@ def lib():
                          ctypes.c_int32, _vp, ctypes.POINTER(GsOptions), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                          ctypes.c_size_t, _vp]
     L.gs_vjp.restype = ctypes.c_int
+    L.gs_jvp.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                         ctypes.c_int32, _vp, ctypes.POINTER(GsOptions), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                         _vp, _vp, ctypes.c_size_t, _vp]
+    L.gs_jvp.restype = ctypes.c_int
     L.gs_vjp_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int32, _vp, ctypes.POINTER(GsOptions), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_vjp_noalloc.restype = ctypes.c_int

@@ -164,6 +164,42 @@ def vjp(system, y0, params, t0, t1, saveat, rtol, atol, dLdy, method="tsit5", pr
     return res
 
 
+def jvp(system, y0, params, t0, t1, saveat, rtol, atol, dy0=None, dparams=None, method="tsit5", precision="fp64",
+        workspace=None, **kw):
+    """Forward sensitivities along m directions (Sec. 2.3): returns dict(y [N,K,d], S [N,K,d,m], status,
+    n_accept, n_reject). dy0 [N,d,m] and dparams [N,p,m] give the directions (None = 0)."""
+    y0 = _dev(y0, None, "y0")
+    dev = y0.device
+    d, p = _abi.dims(system)
+    N = y0.shape[0]
+    y0 = y0.reshape(N, d)
+    params = _dev(params, dev, "params").reshape(N, p) if p else None
+    t0 = _vec(t0, N, dev, "t0")
+    t1 = _vec(t1, N, dev, "t1")
+    saveat = _dev(saveat, dev, "saveat")
+    per_traj = saveat.dim() == 2
+    K = saveat.shape[-1]
+    dy0 = _dev(dy0, dev, "dy0") if dy0 is not None else None
+    dparams = _dev(dparams, dev, "dparams") if dparams is not None else None
+    m = dy0.shape[-1] if dy0 is not None else dparams.shape[-1]
+    if dy0 is not None:
+        dy0 = dy0.reshape(N, d, m)
+    if dparams is not None:
+        dparams = dparams.reshape(N, p, m)
+    opt = _abi.options(method, precision, "persistent", per_traj_saveat=int(per_traj), **kw)
+    nbytes = _abi.lib().gs_workspace_bytes(_sysid(system), N, K, ctypes.byref(opt), 0, 0.0)
+    wsb = _ws(dev, nbytes, workspace)
+    out = dict(y=torch.empty((N, K, d), dtype=torch.float64, device=dev),
+               S=torch.empty((N, K, d, m), dtype=torch.float64, device=dev),
+               status=torch.empty(N, dtype=_i32, device=dev), n_accept=torch.empty(N, dtype=_i32, device=dev),
+               n_reject=torch.empty(N, dtype=_i32, device=dev))
+    _abi.check(_abi.lib().gs_jvp(_sysid(system), N, _ptr(y0), _ptr(params), _ptr(t0), _ptr(t1), float(rtol), float(atol),
+                                 K, _ptr(saveat), ctypes.byref(opt), m, _ptr(dy0), _ptr(dparams), _ptr(out["y"]),
+                                 _ptr(out["S"]), _ptr(out["status"]), _ptr(out["n_accept"]), _ptr(out["n_reject"]),
+                                 _ptr(wsb), wsb.numel(), _stream(dev)))
+    return out
+
+
 def rhs(system, t, y, params=None, w=None, precision="fp64"):
     """f(t, y, theta) and, if w is given, J_y^T w and J_theta^T w, evaluated by the device code."""
     y = _dev(y, None, "y")
@@ -213,3 +249,64 @@ def solve_autograd(system, y0, params, t0, t1, saveat, rtol, atol, **opts):
     t1 = torch.as_tensor(t1, dtype=torch.float64, device=dev).expand(N).contiguous()
     saveat = torch.as_tensor(saveat, dtype=torch.float64, device=dev)
     return GsSolve.apply(y0, params, system, t0, t1, saveat, rtol, atol, opts)
+
+
+class GraphedStep:
+    """A forward solve (optionally recording its tape), an optional loss cotangent and the reverse
+    sweep, captured once into a CUDA graph and replayed. Inputs and outputs are static device tensors:
+    copy new inputs into `inputs[...]` and read `outputs[...]` after `replay()`.
+
+    cotangent(y) -> dL/dy is captured with the solve (it must be made of stream-ordered device ops).
+    The library's launches query occupancy and the device only on the host side, and every kernel
+    argument lives in the captured tensors, so the graph is valid for as long as this object lives.
+    The first call of the library on a device must happen before capture (it is warmed up here)."""
+
+    def __init__(self, system, y0, params, t0, t1, saveat, rtol, atol, cotangent=None, grad=True, tape_slack=1.5,
+                 **opts):
+        dev = y0.device
+        N = y0.shape[0]
+        d, p = _abi.dims(system)
+        self.inputs = dict(y0=y0.detach().clone(), params=(params.detach().clone() if p else None),
+                           t0=_vec(t0, N, dev, "t0").clone(), t1=_vec(t1, N, dev, "t1").clone(),
+                           saveat=_dev(saveat, dev, "saveat").clone())
+        self.system, self.rtol, self.atol, self.opts, self.grad = system, rtol, atol, dict(opts), grad
+        self.cotangent = cotangent
+        self.ws = Workspace(dev)
+        probe = solve(system, self.inputs["y0"], self.inputs["params"], self.inputs["t0"], self.inputs["t1"],
+                      self.inputs["saveat"], rtol, atol, **opts)
+        # the tape is sized once, from these inputs, with headroom for later inputs that take more steps;
+        # trajectories that still do not fit report GS_ST_TAPE_OVERFLOW
+        self.tape_nbytes = (tape_bytes(system, N, n_accept=(probe["n_accept"].double() * tape_slack).ceil().int())
+                            if grad else None)
+        self.outputs = None
+        self._run()  # warm-up outside capture: library load, workspace allocation, occupancy cache
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(self.graph, stream=s):
+                self._run()
+        torch.cuda.current_stream(dev).wait_stream(s)
+
+    def _run(self):
+        i = self.inputs
+        s = solve(self.system, i["y0"], i["params"], i["t0"], i["t1"], i["saveat"], self.rtol, self.atol,
+                  record_tape=self.grad, workspace=self.ws, tape_nbytes=self.tape_nbytes, out=self.outputs and
+                  {k: self.outputs[k] for k in ("y", "status", "n_accept", "n_reject")}, **self.opts)
+        out = dict(s)
+        if self.grad:
+            w = self.cotangent(s["y"]) if self.cotangent is not None else torch.ones_like(s["y"])
+            g = vjp(self.system, i["y0"], i["params"], i["t0"], i["t1"], i["saveat"], self.rtol, self.atol, w,
+                    workspace=self.ws, reuse_tape=s, **self.opts)
+            out.update(dLdy0=g["dLdy0"], dLdparams=g["dLdparams"])
+        if self.outputs is None:
+            self.outputs = out
+        else:
+            for k, v in out.items():
+                if v.data_ptr() != self.outputs[k].data_ptr():
+                    self.outputs[k].copy_(v)
+
+    def replay(self):
+        self.graph.replay()
+        return self.outputs

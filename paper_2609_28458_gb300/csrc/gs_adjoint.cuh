@@ -94,7 +94,8 @@ struct Adjoint {
     }
     return v;
   }
-  __device__ static void load_state(const unsigned char* s, T& tr) {
+  __device__ static void load_state(const unsigned char* s, T& tr) { load_state_raw(s, tr.y, tr.ylo); }
+  __device__ static void load_state_raw(const unsigned char* s, R* yv, R* ylov) {
     if constexpr (F32) {
       float v[2 * D];
       if constexpr ((2 * D) % 4 == 0) {
@@ -110,11 +111,11 @@ struct Adjoint {
         for (int q = 0; q < D; q++) { const float2 a = f2[q]; v[2 * q] = a.x; v[2 * q + 1] = a.y; }
       }
 #pragma unroll
-      for (int i = 0; i < D; i++) { tr.y[i] = v[i]; tr.ylo[i] = v[D + i]; }
+      for (int i = 0; i < D; i++) { yv[i] = v[i]; ylov[i] = v[D + i]; }
     } else {
       const double* f = reinterpret_cast<const double*>(s);
 #pragma unroll
-      for (int i = 0; i < D; i++) tr.y[i] = f[i];
+      for (int i = 0; i < D; i++) yv[i] = f[i];
     }
   }
 
@@ -207,14 +208,24 @@ struct Adjoint {
     const double t0 = tr.t0, t1 = tr.t1;
     const int o = a % kChunk;
     const unsigned char* sp = slot_ptr(pb, chunk, o);
-    const int32_t pchunk = (o == 0 && a > 0) ? prev_chunk(pb, chunk) : chunk;
     const SlotView cur = load_times(sp);
-    SlotView prev;
-    if (a > 0) prev = load_times(slot_ptr(pb, pchunk, o == 0 ? kChunk - 1 : o - 1));
     load_state(sp, tr);
+    const int32_t pchunk = (o == 0 && a > 0) ? prev_chunk(pb, chunk) : chunk;
+    // the times of step a - 1 (valid for a > 0): outputs inside it belong to that step
+    const SlotView prev = a > 0 ? load_times(slot_ptr(pb, pchunk, o == 0 ? kChunk - 1 : o - 1)) : cur;
     Sys::f(tr.stage_time(cur.t), tr.y, tr.p, tr.k1);
+    // does an output inside this step use the dense polynomial (which needs the last, FSAL stage)?
+    bool dense_here = false;
+    if constexpr (Tab::DENSE_POLY) {
+      for (int q = kk; q >= 0; q--) {
+        if (!save_valid(pb, n, q, t0, t1)) continue;
+        const double sq = save_at(pb, n, q);
+        if (sq == t0 || !inside(cur, sq) || (a > 0 && inside(prev, sq))) break;
+        if (!(cur.last && sq == t1)) { dense_here = true; break; }
+      }
+    }
     R k[S][D], Y[S][D], kbar[S][D];
-    tr.stages(cur.t, cur.h, k, Y, S);
+    tr.stages(cur.t, cur.h, k, Y, dense_here ? S : Tab::NREV);
 #pragma unroll
     for (int j = 0; j < S; j++)
 #pragma unroll

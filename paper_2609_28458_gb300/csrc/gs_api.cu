@@ -78,6 +78,16 @@ launch_fn forward_of(int32_t sys, int32_t method) {
     default: return GS_PICK(forward, loghalo);
   }
 }
+typedef cudaError_t (*jvp_fn)(const gs::Problem&, const gs::LaunchCfg&, int);
+jvp_fn jvp_of(int32_t sys, int32_t method) {
+  switch (sys) {
+    case GS_SYS_ISOCHRONE: return GS_PICK(jvp, isochrone);
+    case GS_SYS_MW: return GS_PICK(jvp, mw);
+    case GS_SYS_PRECESSION: return GS_PICK(jvp, precession);
+    case GS_SYS_QUINTESSENCE: return GS_PICK(jvp, quintessence);
+    default: return GS_PICK(jvp, loghalo);
+  }
+}
 launch_fn reverse_of(int32_t sys, int32_t method) {
   switch (sys) {
     case GS_SYS_ISOCHRONE: return GS_PICK(reverse, isochrone);
@@ -276,6 +286,41 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   }
   cudaError_t e = reverse_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "reverse launch");
+  return GS_OK;
+}
+
+int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
+           const double* t1, double rtol, double atol, int32_t K, const double* saveat, const gs_options* opt,
+           int32_t m, const double* dy0, const double* dparams, double* y_out, double* S_out, int32_t* status,
+           int32_t* n_accept, int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  int32_t d, p;
+  int rc = check_common(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, &d, &p);
+  if (rc) return rc;
+  if (m < 1) return fail(GS_ERR_INVALID, "m (number of sensitivity directions) must be >= 1");
+  if (opt->precision == GS_FP32_STAGES)
+    return fail(GS_ERR_INVALID, "gs_jvp runs in GS_FP64 or GS_FP32_DF");
+  if (N > 0 && ((K > 0 && (!y_out || !S_out)) || !status || !n_accept || !n_reject))
+    return fail(GS_ERR_INVALID, "y_out, S_out, status and step counts must not be NULL");
+  if (N == 0) return GS_OK;
+  if (!workspace || workspace_bytes < 256 || reinterpret_cast<uintptr_t>(workspace) % 256 != 0)
+    return fail(GS_ERR_WORKSPACE, "gs_jvp needs a 256-byte aligned workspace of at least 256 bytes");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  gs::Problem pb = make_problem(N, y0, params, t0, t1, rtol, atol, K, saveat, opt);
+  pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
+  pb.queue = static_cast<unsigned int*>(workspace);
+  pb.dy0 = dy0; pb.dp = dparams; pb.S_out = S_out; pb.m_total = m;
+  const int group = opt->method == GS_VERN7 ? 1 : 4;
+  gs::LaunchCfg c{opt->method, opt->precision, GS_KERNEL_PERSISTENT, opt->block_size, s};
+  for (int32_t off = 0; off < m;) {
+    const int32_t left = m - off;
+    const int mt = left >= 4 && group >= 4 ? 4 : (left >= 2 && group >= 2 ? 2 : 1);
+    pb.m_off = off;
+    cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = jvp_of(system, opt->method)(pb, c, mt);
+    if (e != cudaSuccess) return cuda_fail(e, "jvp launch");
+    off += mt;
+  }
   return GS_OK;
 }
 

@@ -28,11 +28,17 @@ struct LaunchCfg {
 // 7-stage pairs on states of at most 6 components: the FP32-pipe forward fits 5 blocks
 // (96 registers), the FP64-control forward 4, the FP32 reverse 3 (<= 168), without spills. FP64,
 // Verner 7 and the 9-component precession state keep the compiler's choice.
-template <template <class> class SysT, class Tab, int PM>
+#ifndef GS_FWD_BLOCKS_FP32DF
+#define GS_FWD_BLOCKS_FP32DF 5
+#endif
+#ifndef GS_REV_BLOCKS_FP32
+#define GS_REV_BLOCKS_FP32 3
+#endif
+template <template <class> class SysT, class Tab, int PM, int MT = 0>
 struct Occupancy {
-  static constexpr bool small = Tab::S <= 7 && SysT<float>::D <= 6;
-  static constexpr int fwd = (PM == 2 && small) ? 5 : (PM == 1 && small) ? 4 : 1;
-  static constexpr int rev = (PM != 0 && small) ? 3 : 1;
+  static constexpr bool small = Tab::S <= 7 && SysT<float>::D <= 6 && MT == 0;
+  static constexpr int fwd = (PM == 2 && small) ? GS_FWD_BLOCKS_FP32DF : (PM == 1 && small) ? 4 : 1;
+  static constexpr int rev = (PM != 0 && small) ? GS_REV_BLOCKS_FP32 : 1;
 };
 
 template <template <class> class SysT, class Tab, int PM>
@@ -45,9 +51,9 @@ __global__ void __launch_bounds__(128) k_plain(const Problem pb) {
   tr.finish(pb);
 }
 
-template <template <class> class SysT, class Tab, int PM>
-__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::fwd)) k_persist(const Problem pb) {
-  Traj<SysT, Tab, PM> tr;
+template <template <class> class SysT, class Tab, int PM, int MT = 0>
+__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_persist(const Problem pb) {
+  Traj<SysT, Tab, PM, MT> tr;
   bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -201,6 +207,40 @@ cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
   return cudaGetLastError();
 }
 
+// forward solve carrying MT sensitivity directions (persistent kernel)
+template <template <class> class SysT, class Tab, int PM, int MT>
+cudaError_t launch_jvp_t(const Problem& pb, const LaunchCfg& c) {
+  const int block = c.block > 0 ? c.block : 128;
+  auto kern = k_persist<SysT, Tab, PM, MT>;
+  long long grid = persistent_grid(kern, block);
+  const long long need = (pb.N + block - 1) / block;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
+  return cudaGetLastError();
+}
+// directions per launch: up to 4 for the 7-stage pairs, 1 for Verner 7 (its 10 stages of duals would
+// not fit the register file)
+template <class Tab>
+constexpr int max_jvp_group() { return Tab::S <= 7 ? 4 : 1; }
+
+template <template <class> class SysT, class Tab, int PM>
+cudaError_t launch_jvp_p(const Problem& pb, const LaunchCfg& c, int mt) {
+  if constexpr (Tab::S <= 7) {
+    switch (mt) {
+      case 1: return launch_jvp_t<SysT, Tab, PM, 1>(pb, c);
+      case 2: return launch_jvp_t<SysT, Tab, PM, 2>(pb, c);
+      default: return launch_jvp_t<SysT, Tab, PM, 4>(pb, c);
+    }
+  } else {
+    return launch_jvp_t<SysT, Tab, PM, 1>(pb, c);
+  }
+}
+template <template <class> class SysT, class Tab>
+cudaError_t launch_jvp_m(const Problem& pb, const LaunchCfg& c, int mt) {
+  return c.precision == 0 ? launch_jvp_p<SysT, Tab, 0>(pb, c, mt) : launch_jvp_p<SysT, Tab, 2>(pb, c, mt);
+}
+
 template <template <class> class SysT, class Tab>
 cudaError_t launch_forward_m(const Problem& pb, const LaunchCfg& c) {
   switch (c.precision) {
@@ -233,7 +273,8 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
 // evaluator of each system (in its Tsit5 unit)
 #define GS_DECLARE_METHOD(name, Tab)                                      \
   cudaError_t forward_##name##_##Tab(const Problem& pb, const LaunchCfg& c); \
-  cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c);
+  cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c); \
+  cudaError_t jvp_##name##_##Tab(const Problem& pb, const LaunchCfg& c, int mt);
 #define GS_DECLARE_SYSTEM(name)                                                                         \
   GS_DECLARE_METHOD(name, Tsit5)                                                                        \
   GS_DECLARE_METHOD(name, Dopri5)                                                                       \
@@ -247,6 +288,9 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
   }                                                                                                      \
   cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c) {                             \
     return launch_reverse_m<SysT, Tab>(pb, c);                                                           \
+  }                                                                                                      \
+  cudaError_t jvp_##name##_##Tab(const Problem& pb, const LaunchCfg& c, int mt) {                         \
+    return launch_jvp_m<SysT, Tab>(pb, c, mt);                                                           \
   }
 #define GS_DEFINE_RHS(name, SysT)                                                                         \
   cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p,  \

@@ -9,7 +9,8 @@
 // Precision mode PM:
 //  0  FP64: every operation in FP64.
 //  1  FP32 stages: stage vectors, right-hand sides and dense outputs in FP32; the state is a
-//     compensated FP32 pair (hi + lo, updated with an error-free TwoSum); the squares of the scaled
+//     compensated FP32 pair (hi + lo, updated with an error-free TwoSum; stage states are formed
+//     from the high part, whose rounding they share anyway); the squares of the scaled
 //     errors are accumulated in FP64; t is FP64 with Kahan compensation; h, the accept test and the
 //     step-size update are FP64, with the controller's power taken in FP32 (it only scales a
 //     proposal that is then clamped to [alpha_min, alpha_max]).
@@ -28,6 +29,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "gs_dual.cuh"
 #include "gs_systems.cuh"
 #include "gs_tableaux.cuh"
 
@@ -73,6 +75,12 @@ struct Problem {
   int32_t record;
   Tape tape;
   unsigned int* queue;  // persistent kernel work counter
+  // forward sensitivities: seeds dy0 [N, d, m_total] and dp [N, p, m_total] (either may be null),
+  // output S [N, K, d, m_total]; a launch handles the directions m_off .. m_off + MT - 1
+  const double* dy0;
+  const double* dp;
+  double* S_out;
+  int32_t m_total, m_off;
   // adjoint
   const double* dLdy;
   double* dLdy0;
@@ -104,6 +112,24 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
 
 constexpr float kEps48 = 3.5527136788005009e-15f;  // 2^-48: unit roundoff of an FP32 pair
 
+// value part and derivative part m of a plain real (derivative 0) or a dual number
+__device__ __forceinline__ float dpart(float, int) { return 0.0f; }
+__device__ __forceinline__ double dpart(double, int) { return 0.0; }
+template <class R, int M> __device__ __forceinline__ R dpart(const Dual<R, M>& x, int m) { return x.d[m]; }
+
+// new state y + incr of an FP32 mode: the value is split error-free into (hi, lo); derivative parts
+// (forward sensitivities) are carried by hi and need no compensation
+__device__ __forceinline__ void state_update(float y, float incr, float& hi, float& lo) {
+  two_sum(y, incr, hi, lo);
+}
+template <int M>
+__device__ __forceinline__ void state_update(const Dual<float, M>& y, const Dual<float, M>& incr, Dual<float, M>& hi,
+                                             float& lo) {
+  two_sum(y.v, incr.v, hi.v, lo);
+#pragma unroll
+  for (int m = 0; m < M; m++) hi.d[m] = y.d[m] + incr.d[m];
+}
+
 template <int PM>
 struct PrecTraits {
   static constexpr bool F32 = PM != 0;
@@ -111,12 +137,16 @@ struct PrecTraits {
   using R = typename std::conditional<F32, float, double>::type;
 };
 
-template <template <class> class SysT, class Tab, int PM>
+// MT: number of forward-sensitivity directions carried with the state (0: none). With MT > 0 every
+// stage quantity is a Dual<R, MT>, so f evaluated on it returns k_j and J_y S_j + J_theta dtheta at once
+// (Sec. 2.3, Eq. sens; Appendix A, Eq. stage-sens); step control uses the value parts only.
+template <template <class> class SysT, class Tab, int PM, int MT = 0>
 struct Traj {
   static constexpr bool F32 = PrecTraits<PM>::F32;
   static constexpr bool DF = PrecTraits<PM>::DF;
   using R = typename PrecTraits<PM>::R;
-  using Sys = SysT<R>;
+  using T = typename std::conditional<(MT > 0), Dual<R, (MT > 0 ? MT : 1)>, R>::type;
+  using Sys = SysT<T>;
   static constexpr int D = Sys::D, NP = Sys::P, S = Tab::S;
   static constexpr int NPA = NP > 0 ? NP : 1;
   static constexpr int DL = F32 ? D : 1;
@@ -130,10 +160,10 @@ struct Traj {
                 "tape slots must stay 16-byte aligned");
   static_assert(8 * D <= kTailOff, "state part of a slot overlaps its tail");
 
-  R y[D];     // state (FP64) / high part (FP32)
+  T y[D];     // state (FP64) / high part (FP32), with its sensitivities when MT > 0
   R ylo[DL];  // low part (FP32)
-  R k1[D];    // f(t, y): the first stage of the next attempt
-  R p[NPA];
+  T k1[D];    // f(t, y): the first stage of the next attempt
+  T p[NPA];
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
   float th, tl, hf, t1h, t1l, svh, svl;   // PM 2
   float atolf, rtolf, lerr_prev;          // PM 1, 2
@@ -144,22 +174,57 @@ struct Traj {
   __device__ __forceinline__ R stage_time(double ts) const { return R(ts); }
 
   __device__ __forceinline__ double yval(int i) const {
-    if constexpr (F32) return double(y[i]) + double(ylo[i]);
-    else return y[i];
+    if constexpr (F32) return double(val(y[i])) + double(ylo[i]);
+    else return double(val(y[i]));
   }
 
-  __device__ void write_out(const Problem& pb, int k, const R* hi, const R* lo) {
+  // y(t_k) = hi + lo (FP32 modes) or hi (FP64), and its sensitivities when MT > 0
+  template <class L>
+  __device__ void write_out(const Problem& pb, int k, const T* hi, const L* lo) {
     double* o = pb.y_out + (n * pb.K + k) * D;
 #pragma unroll
     for (int i = 0; i < D; i++) {
-      if constexpr (F32) o[i] = double(hi[i]) + double(lo[i]);
-      else o[i] = hi[i];
+      if constexpr (F32) o[i] = double(val(hi[i])) + double(val(lo[i]));
+      else o[i] = double(val(hi[i]));
+    }
+    if constexpr (MT > 0) {
+      double* so = pb.S_out + (n * pb.K + k) * (long long)D * pb.m_total + pb.m_off;
+#pragma unroll
+      for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+          if constexpr (F32) so[i * pb.m_total + m] = double(dpart(hi[i], m)) + double(dpart(lo[i], m));
+          else so[i * pb.m_total + m] = double(dpart(hi[i], m));
+        }
     }
   }
   __device__ void write_nan(const Problem& pb, int k) {
+    const double nanv = __longlong_as_double(0x7ff8000000000000LL);
     double* o = pb.y_out + (n * pb.K + k) * D;
 #pragma unroll
-    for (int i = 0; i < D; i++) o[i] = __longlong_as_double(0x7ff8000000000000LL);
+    for (int i = 0; i < D; i++) o[i] = nanv;
+    if constexpr (MT > 0) {
+      double* so = pb.S_out + (n * pb.K + k) * (long long)D * pb.m_total + pb.m_off;
+#pragma unroll
+      for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int m = 0; m < MT; m++) so[i * pb.m_total + m] = nanv;
+    }
+  }
+
+  // output k is y0 exactly (and its sensitivity the seed dy0)
+  __device__ void write_y0(const Problem& pb, int k, const double* y0d) {
+    double* o = pb.y_out + (n * pb.K + k) * D;
+#pragma unroll
+    for (int i = 0; i < D; i++) o[i] = y0d[i];
+    if constexpr (MT > 0) {
+      double* so = pb.S_out + (n * pb.K + k) * (long long)D * pb.m_total + pb.m_off;
+#pragma unroll
+      for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int m = 0; m < MT; m++)
+          so[i * pb.m_total + m] = pb.dy0 ? pb.dy0[(n * D + i) * (long long)pb.m_total + pb.m_off + m] : 0.0;
+    }
   }
 
   // cache the output time of index kk (and whether it is used)
@@ -181,14 +246,14 @@ struct Traj {
       sc[i] = pb.atol + pb.rtol * fabs(yi);
       const double r0 = yi / sc[i];
       d0 += r0 * r0;
-      const double r1 = double(k1[i]) / sc[i];
+      const double r1 = double(val(k1[i])) / sc[i];
       d1 += r1 * r1;
     }
     d0 = sqrt(d0 / D);
     d1 = sqrt(d1 / D);
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * (d0 / d1);
     if (h0 > t1 - t0) h0 = t1 - t0;
-    R y1[D], f1[D];
+    T y1[D], f1[D];
 #pragma unroll
     for (int i = 0; i < D; i++) {
       if constexpr (F32) y1[i] = y[i] + (ylo[i] + R(h0) * k1[i]);
@@ -198,7 +263,7 @@ struct Traj {
     double d2 = 0.0;
 #pragma unroll
     for (int i = 0; i < D; i++) {
-      const double r = (double(f1[i]) - double(k1[i])) / sc[i];
+      const double r = (double(val(f1[i])) - double(val(k1[i]))) / sc[i];
       d2 += r * r;
     }
     d2 = sqrt(d2 / D) / h0;
@@ -222,32 +287,41 @@ struct Traj {
       y0d[i] = pb.y0[n * D + i];
       fin = fin && isfinite(y0d[i]);
       if constexpr (F32) {
-        y[i] = float(y0d[i]);
-        ylo[i] = float(y0d[i] - double(y[i]));
+        const float hi = float(y0d[i]);
+        y[i] = T(hi);
+        ylo[i] = float(y0d[i] - double(hi));
       } else {
-        y[i] = y0d[i];
+        y[i] = T(y0d[i]);
       }
     }
 #pragma unroll
     for (int q = 0; q < NP; q++) {
       const double pv = pb.params[n * NP + q];
       fin = fin && isfinite(pv);
-      p[q] = R(pv);
+      p[q] = T(R(pv));
     }
-    if (NP == 0) p[0] = R(0);
+    if (NP == 0) p[0] = T(R(0));
+    if constexpr (MT > 0) {  // sensitivity seeds: S(t0) = dy0, parameter directions dtheta
+#pragma unroll
+      for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int m = 0; m < MT; m++)
+          y[i].d[m] = pb.dy0 ? R(pb.dy0[(n * D + i) * (long long)pb.m_total + pb.m_off + m]) : R(0);
+#pragma unroll
+      for (int q = 0; q < NP; q++)
+#pragma unroll
+        for (int m = 0; m < MT; m++)
+          p[q].d[m] = pb.dp ? R(pb.dp[(n * NP + q) * (long long)pb.m_total + pb.m_off + m]) : R(0);
+    }
     if (!fin) {
       status = ST_NONFINITE;
       failed = true;
       done = true;
       return;
     }
-    if (!(t1 > t0)) {  // empty or reversed interval: every output is y0
+    if (!(t1 > t0)) {  // empty or reversed interval: every output is y0 (and S = dy0)
       status = ST_EMPTY;
-      for (int k = 0; k < pb.K; k++) {
-        double* o = pb.y_out + (n * pb.K + k) * D;
-#pragma unroll
-        for (int i = 0; i < D; i++) o[i] = y0d[i];
-      }
+      for (int k = 0; k < pb.K; k++) write_y0(pb, k, y0d);
       done = true;
       return;
     }
@@ -258,11 +332,7 @@ struct Traj {
       }
     }
     while (kk < pb.K && (!save_valid(pb, n, kk, t0, t1) || save_at(pb, n, kk) == t0)) {
-      if (save_valid(pb, n, kk, t0, t1)) {
-        double* o = pb.y_out + (n * pb.K + kk) * D;
-#pragma unroll
-        for (int i = 0; i < D; i++) o[i] = y0d[i];
-      }
+      if (save_valid(pb, n, kk, t0, t1)) write_y0(pb, kk, y0d);
       kk++;
     }
     load_sv(pb);
@@ -283,21 +353,21 @@ struct Traj {
 
   // Stages of one step of length hh from (tt, y): Eq. rk. k[0] = k1 on entry.
   // Y[j] receives the state at which stage j was evaluated (Y[0] = y).
-  __device__ __forceinline__ void stages(double tt, double hh, R (*k)[D], R (*Y)[D], int nst) const {
+  __device__ __forceinline__ void stages(double tt, double hh, T (*k)[D], T (*Y)[D], int nst) const {
     const R hr = R(hh);
 #pragma unroll
     for (int i = 0; i < D; i++) { k[0][i] = k1[i]; if (Y) Y[0][i] = y[i]; }
 #pragma unroll
     for (int j = 1; j < S; j++) {
       if (j < nst) {
-        R Yj[D];
+        T Yj[D];
 #pragma unroll
         for (int i = 0; i < D; i++) {
-          R acc = R(0);
+          T acc = T(R(0));
 #pragma unroll
           for (int l = 0; l < j; l++)
             if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
-          if constexpr (F32) Yj[i] = y[i] + (ylo[i] + hr * acc);
+          if constexpr (F32) Yj[i] = y[i] + hr * acc;
           else Yj[i] = y[i] + hh * acc;
           if (Y) Y[j][i] = Yj[i];
         }
@@ -309,37 +379,38 @@ struct Traj {
 
   // Solution at tt + sig*hh inside the accepted step just taken (Eq. dense; Verner 7: shortened
   // step from the start of the step). k holds the step's stages.
-  __device__ void dense_point(double tt, double hh, R sig, R (*k)[D], R* hi, R* lo) const {
+  __device__ void dense_point(double tt, double hh, R sig, T (*k)[D], T* hi, T* lo) const {
     if constexpr (Tab::DENSE_POLY) {
       R w[S];
       Tab::dense(sig, w);
       const R hr = R(hh);
 #pragma unroll
       for (int i = 0; i < D; i++) {
-        R acc = R(0);
+        T acc = T(R(0));
 #pragma unroll
         for (int j = 0; j < S; j++) acc = acc + w[j] * k[j][i];
         if constexpr (F32) { hi[i] = y[i]; lo[i] = ylo[i] + hr * acc; }
-        else { hi[i] = y[i] + hh * acc; lo[i] = R(0); }
+        else { hi[i] = y[i] + hh * acc; lo[i] = T(R(0)); }
       }
     } else {
-      R ks[S][D];
+      T ks[S][D];
       const double hs = double(sig) * hh;
       stages(tt, hs, ks, nullptr, Tab::NREV);
       const R hr = R(hs);
 #pragma unroll
       for (int i = 0; i < D; i++) {
-        R acc = R(0);
+        T acc = T(R(0));
 #pragma unroll
         for (int j = 0; j < Tab::NREV; j++)
           if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * ks[j][i];
         if constexpr (F32) { hi[i] = y[i]; lo[i] = ylo[i] + hr * acc; }
-        else { hi[i] = y[i] + hs * acc; lo[i] = R(0); }
+        else { hi[i] = y[i] + hs * acc; lo[i] = T(R(0)); }
       }
     }
   }
 
   __device__ void record_slot(const Problem& pb, bool last, R hstep) {
+    if constexpr (MT == 0) {  // the tape is recorded by the solve without sensitivities
     const int a = nacc - 1;  // index of the step just accepted
     if (!rec_ok) return;
     const int o = a % kChunk;
@@ -376,6 +447,7 @@ struct Traj {
     } else {
       double* tail = reinterpret_cast<double*>(slot + kTailOff);
       tail[0] = t; tail[1] = tc; tail[2] = h; tail[3] = last ? 1.0 : 0.0;
+    }
     }
   }
 
@@ -440,20 +512,22 @@ struct Traj {
       hr = R(h);
     }
     // ---- stages 2..S (the last one is the new state for FSAL pairs), Eq. rk
-    R k[S][D];
-    R Ylast[D];
+    T k[S][D];
+    T Ylast[D];
 #pragma unroll
     for (int i = 0; i < D; i++) k[0][i] = k1[i];
 #pragma unroll
     for (int j = 1; j < S; j++) {
-      R Yj[D];
+      T Yj[D];
 #pragma unroll
       for (int i = 0; i < D; i++) {
-        R acc = R(0);
+        T acc = T(R(0));
 #pragma unroll
         for (int l = 0; l < j; l++)
           if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
-        if constexpr (F32) Yj[i] = y[i] + (ylo[i] + hr * acc);
+        // FP32 modes: the stage state is y_hi + h sum a k; the low part of the state only enters the
+        // update of the state itself (below), its effect on a stage is below the stage's FP32 rounding
+        if constexpr (F32) Yj[i] = y[i] + hr * acc;
         else Yj[i] = y[i] + h * acc;
         if (j == S - 1) Ylast[i] = Yj[i];
       }
@@ -461,18 +535,19 @@ struct Traj {
       else Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
     }
     // ---- new state: y + h sum b_j k_j
-    R ynew[D], ynlo[DL];
+    T ynew[D];
+    R ynlo[DL];
 #pragma unroll
     for (int i = 0; i < D; i++) {
       if constexpr (Tab::FSAL && !F32) {
         ynew[i] = Ylast[i];
       } else {
-        R acc = R(0);
+        T acc = T(R(0));
 #pragma unroll
         for (int j = 0; j < S; j++)
           if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * k[j][i];
         if constexpr (F32) {
-          two_sum(y[i], ylo[i] + hr * acc, ynew[i], ynlo[i]);
+          state_update(y[i], ylo[i] + hr * acc, ynew[i], ynlo[i]);
         } else {
           ynew[i] = y[i] + h * acc;
         }
@@ -490,9 +565,9 @@ struct Traj {
         double acc = 0.0;
 #pragma unroll
         for (int j = 0; j < S; j++)
-          if (Tab::bt(j) != 0.0) acc = acc + Tab::bt(j) * k[j][i];
+          if (Tab::bt(j) != 0.0) acc = acc + Tab::bt(j) * val(k[j][i]);
         const double e = h * acc;
-        const double a = fabs(y[i]), b = fabs(ynew[i]);
+        const double a = fabs(val(y[i])), b = fabs(val(ynew[i]));
         const double sc = pb.atol + pb.rtol * (a > b ? a : b);
         const double r = e / sc;
         sq += r * r;
@@ -509,9 +584,9 @@ struct Traj {
         R acc = R(0);
 #pragma unroll
         for (int j = 0; j < S; j++)
-          if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * k[j][i];
+          if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * val(k[j][i]);
         const R e = hr * acc;
-        const R a = fabsf(y[i]), b = fabsf(ynew[i]);
+        const R a = fabsf(val(y[i])), b = fabsf(val(ynew[i]));
         const R sc = atolf + rtolf * (a > b ? a : b);
         const Acc r = Acc(__fdividef(e, sc));
         sq += r * r;
@@ -543,9 +618,10 @@ struct Traj {
           sig = R(sg);
         }
         if (at_end) {
-          write_out(pb, kk, ynew, F32 ? ynlo : ynew);
+          if constexpr (F32) write_out(pb, kk, ynew, ynlo);
+          else write_out(pb, kk, ynew, ynew);
         } else if (inside) {
-          R hi[D], lo[D];
+          T hi[D], lo[D];
           if constexpr (DF) dense_point(double(th) + double(tl), double(hf), sig, k, hi, lo);
           else dense_point(t, h, sig, k, hi, lo);
           write_out(pb, kk, hi, lo);
