@@ -197,7 +197,7 @@ def run_gpu(args):
     def make(prec, rtol, kernel="persistent"):
         ws = api.Workspace(dev)
         probe = api.solve("mw", y0, pr, t0, t1, sv, rtol, rtol, precision=prec, kernel=kernel)
-        nbytes = api.tape_bytes("mw", N, n_accept=probe["n_accept"])
+        nbytes = api.tape_bytes("mw", N, n_accept=probe["n_accept"], precision=prec)
 
         def step():  # forward with tape, loss cotangent, reverse
             s = api.solve("mw", y0, pr, t0, t1, sv, rtol, rtol, precision=prec, kernel=kernel, record_tape=True,
@@ -314,7 +314,7 @@ def run_gpu(args):
     out_p = torch.empty((N, 4), dtype=torch.float64).pin_memory()
     dbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
     ws_e2e = api.Workspace(dev)
-    tape_nb = api.tape_bytes("mw", N, n_accept=s["n_accept"])
+    tape_nb = api.tape_bytes("mw", N, n_accept=s["n_accept"], precision=HEAD_PREC)
 
     def e2e_step():
         for k in host:
@@ -488,7 +488,7 @@ def run_workload(args):
                "attempts_mean": float((s["n_accept"] + s["n_reject"]).double().mean())}
         if grad:
             ws = api.Workspace(dev)
-            nb = api.tape_bytes(system, e.n, n_accept=s["n_accept"])
+            nb = api.tape_bytes(system, e.n, n_accept=s["n_accept"], precision=prec)
             w = torch.ones_like(s["y"])
 
             def fg():
@@ -531,7 +531,7 @@ def run_case(args):
     else:
         ws = api.Workspace(dev)
         probe = api.solve("mw", y0, pr, t0, t1, sv, args.rtol, args.rtol, **kw)
-        nb = api.tape_bytes("mw", args.n, n_accept=probe["n_accept"])
+        nb = api.tape_bytes("mw", args.n, n_accept=probe["n_accept"], precision=args.precision)
         for _ in range(2):
             s = api.solve("mw", y0, pr, t0, t1, sv, args.rtol, args.rtol, record_tape=True, workspace=ws,
                           tape_nbytes=nb, **kw)

@@ -93,7 +93,8 @@ typedef struct {
   int32_t record_tape;     /* gs_solve: record the accepted steps into the workspace  */
   int32_t reuse_tape;      /* gs_vjp: reverse the tape recorded by the preceding
                               gs_solve (same inputs and options) instead of re-solving */
-  int32_t tape_capacity;   /* max accepted steps recorded per trajectory (65536)      */
+  int32_t tape_capacity;   /* max accepted steps recorded per trajectory (1e6); a
+                              trajectory with more gets GS_ST_TAPE_OVERFLOW            */
   int32_t reserved;
 } gs_options;
 
@@ -130,8 +131,11 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
  *  recording gs_solve (status gains GS_ST_TAPE_OVERFLOW there); the forward solve is not re-run.
  *  The workspace holds the step tape: per accepted step the state at its start, its time and
  *  its length, in chunks taken from a pool by an atomic counter. Layout: a 256-byte header, int32
- *  head[N] and n_rec[N] (each padded to 256 bytes), then chunks of 16 + 32 * slot bytes with
- *  slot = roundup16(8 d) + 32; a trajectory with n accepted steps uses ceil(n / 32) chunks.
+ *  head[N] and n_rec[N] (each padded to 256 bytes), then chunks of 16 + 32 * slot bytes; a
+ *  trajectory with n accepted steps uses ceil(n / 32) chunks. slot = roundup16(state) + tail:
+ *  GS_FP64 state 8 d bytes (FP64), tail 32 (t, tc, h, flag as FP64); GS_FP32_STAGES state 4 d (the
+ *  FP32 high part, from which the stages are recomputed), tail 32; GS_FP32_DF state 4 d, tail 16
+ *  (time pair, h, flag as FP32).
  */
 int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
            const double* t1, double rtol, double atol, int32_t K, const double* saveat,
@@ -161,9 +165,9 @@ int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* pa
 
 /* Workspace bytes for N trajectories. for_vjp = 0: the persistent kernel's counter only.
  * for_vjp != 0: room for a step tape of `steps_hint` accepted steps per trajectory on average
- * (rounded up to whole chunks per trajectory), plus the chunk table sized by
- * opt->tape_capacity. A smaller workspace is accepted; trajectories whose steps no longer fit
- * get GS_ST_TAPE_OVERFLOW. */
+ * (rounded up to whole chunks per trajectory, plus one), in the slot size of opt->precision
+ * (FP64 when opt is NULL). A smaller workspace is accepted; trajectories whose steps no longer
+ * fit get GS_ST_TAPE_OVERFLOW. */
 size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
                           double steps_hint);
 

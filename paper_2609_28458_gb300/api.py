@@ -72,12 +72,16 @@ def _ws(device, nbytes, ws):
     return ws.get(nbytes)[: int(nbytes)]
 
 
-def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None):
-    """Workspace bytes for a tape: exact from per-trajectory accepted-step counts, else from a hint."""
+def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None, precision="fp64"):
+    """Workspace bytes for a tape: exact from per-trajectory accepted-step counts, else from a hint.
+    The slot size depends on the precision mode (opt.precision, else `precision`)."""
     d, _ = _abi.dims(system)
-    opt = opt or _abi.options()
+    opt = opt or _abi.options(precision=precision)
     fixed = _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 0, 0.0)
-    chunk = 16 + 32 * ((8 * d + 15) // 16 * 16 + 32)  # chunk header + 32 slots (gs.h)
+    prec = opt.precision
+    state = (8 if prec == _abi.PRECISIONS["fp64"] else 4) * d
+    slot = (state + 15) // 16 * 16 + (16 if prec == _abi.PRECISIONS["fp32df"] else 32)
+    chunk = 16 + 32 * slot  # chunk header + 32 slots (gs.h)
     if n_accept is not None:
         chunks = int(((n_accept.to(torch.int64) + 31) // 32).sum().item()) + 1
         return fixed + chunks * chunk
@@ -276,8 +280,8 @@ class GraphedStep:
                       self.inputs["saveat"], rtol, atol, **opts)
         # the tape is sized once, from these inputs, with headroom for later inputs that take more steps;
         # trajectories that still do not fit report GS_ST_TAPE_OVERFLOW
-        self.tape_nbytes = (tape_bytes(system, N, n_accept=(probe["n_accept"].double() * tape_slack).ceil().int())
-                            if grad else None)
+        self.tape_nbytes = (tape_bytes(system, N, n_accept=(probe["n_accept"].double() * tape_slack).ceil().int(),
+                                       precision=opts.get("precision", "fp64")) if grad else None)
         self.outputs = None
         self._run()  # warm-up outside capture: library load, workspace allocation, occupancy cache
         torch.cuda.synchronize(dev)

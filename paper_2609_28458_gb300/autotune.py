@@ -91,7 +91,7 @@ def tune(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precisi
         nbytes = None
         if fwd_grad:
             probe = api.solve(system, Y0, P, T0, T1, SV, rtol, atol, method=method, precision=precision)
-            nbytes = api.tape_bytes(system, Y0.shape[0], n_accept=probe["n_accept"])
+            nbytes = api.tape_bytes(system, Y0.shape[0], n_accept=probe["n_accept"], precision=precision)
     t = time.time()
     timings = {c: timer(*c) for c in CANDIDATES}
     kernel, block = pick(timings)

@@ -94,28 +94,32 @@ struct Adjoint {
     }
     return v;
   }
-  __device__ static void load_state(const unsigned char* s, T& tr) { load_state_raw(s, tr.y, tr.ylo); }
-  __device__ static void load_state_raw(const unsigned char* s, R* yv, R* ylov) {
+  // the state at the step's start; in the FP32 modes its high part (the low part is not recorded:
+  // the stages are recomputed from the high part, as in the forward attempt)
+  __device__ static void load_state(const unsigned char* s, T& tr) {
     if constexpr (F32) {
-      float v[2 * D];
-      if constexpr ((2 * D) % 4 == 0) {
+      if constexpr (D % 4 == 0) {
         const float4* f4 = reinterpret_cast<const float4*>(s);
 #pragma unroll
-        for (int q = 0; q < (2 * D) / 4; q++) {
+        for (int q = 0; q < D / 4; q++) {
           const float4 a = f4[q];
-          v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+          tr.y[4 * q] = a.x; tr.y[4 * q + 1] = a.y; tr.y[4 * q + 2] = a.z; tr.y[4 * q + 3] = a.w;
         }
-      } else {
+      } else if constexpr (D % 2 == 0) {
         const float2* f2 = reinterpret_cast<const float2*>(s);
 #pragma unroll
-        for (int q = 0; q < D; q++) { const float2 a = f2[q]; v[2 * q] = a.x; v[2 * q + 1] = a.y; }
+        for (int q = 0; q < D / 2; q++) { const float2 a = f2[q]; tr.y[2 * q] = a.x; tr.y[2 * q + 1] = a.y; }
+      } else {
+        const float* f = reinterpret_cast<const float*>(s);
+#pragma unroll
+        for (int i = 0; i < D; i++) tr.y[i] = f[i];
       }
 #pragma unroll
-      for (int i = 0; i < D; i++) { yv[i] = v[i]; ylov[i] = v[D + i]; }
+      for (int i = 0; i < D; i++) tr.ylo[i] = 0.0f;
     } else {
       const double* f = reinterpret_cast<const double*>(s);
 #pragma unroll
-      for (int i = 0; i < D; i++) yv[i] = f[i];
+      for (int i = 0; i < D; i++) tr.y[i] = f[i];
     }
   }
 

@@ -47,8 +47,13 @@ int order_of(int32_t method) { return method == GS_VERN7 ? 7 : 5; }
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // bytes of one tape slot: state (8 d bytes in every precision) padded to 16 bytes + a 32-byte tail
-long long slot_bytes(int32_t d) { return (8LL * d + 15) / 16 * 16 + 32; }
-long long chunk_bytes(int32_t d) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d); }
+// tape slot: the state at the step's start (FP64, or its FP32 high part), padded to 16 bytes,
+// then the times: t, tc, h, flag as FP64 (32 bytes), or th, tl, h, flag as FP32 (16 bytes, PM 2)
+long long slot_bytes(int32_t d, int32_t prec) {
+  const long long state = (prec == GS_FP64 ? 8LL : 4LL) * d;
+  return (state + 15) / 16 * 16 + (prec == GS_FP32_DF ? 16 : 32);
+}
+long long chunk_bytes(int32_t d, int32_t prec) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d, prec); }
 
 // workspace: [0,256) header (queue counter at 0, pool counter at 8) | head[N] | n_rec[N] | pool
 struct Layout {
@@ -147,17 +152,20 @@ gs::Problem make_problem(int64_t N, const double* y0, const double* params, cons
   return pb;
 }
 
-int set_tape(gs::Problem& pb, int32_t d, int64_t N, void* ws, size_t ws_bytes) {
+int set_tape(gs::Problem& pb, int32_t d, int32_t prec, int32_t opt_cap, int64_t N, void* ws, size_t ws_bytes) {
+  if (opt_cap <= 0) return fail(GS_ERR_INVALID, "tape_capacity must be positive");
   Layout L = layout(N);
+  const long long cb = chunk_bytes(d, prec);
   if (!ws) return fail(GS_ERR_WORKSPACE, "this call needs a workspace (see gs_workspace_bytes)");
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(GS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
-  if (ws_bytes < L.total_fixed + size_t(chunk_bytes(d)))
+  if (ws_bytes < L.total_fixed + size_t(cb))
     return fail(GS_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu needed for N = %lld", ws_bytes,
-                size_t(L.total_fixed + chunk_bytes(d)), (long long)N);
+                size_t(L.total_fixed + cb), (long long)N);
   unsigned char* base = static_cast<unsigned char*>(ws);
   pb.tape.pool = base + L.pool;
-  pb.tape.chunk_bytes = chunk_bytes(d);
-  pb.tape.pool_chunks = (long long)((ws_bytes - L.pool) / size_t(chunk_bytes(d)));
+  pb.tape.chunk_bytes = cb;
+  pb.tape.cap = opt_cap;
+  pb.tape.pool_chunks = (long long)((ws_bytes - L.pool) / size_t(cb));
   if (pb.tape.pool_chunks > 0x7fffffffLL) pb.tape.pool_chunks = 0x7fffffffLL;
   pb.tape.pool_next = reinterpret_cast<unsigned long long*>(base + 8);
   pb.tape.head = reinterpret_cast<int32_t*>(base + L.head);
@@ -191,7 +199,7 @@ void gs_default_options(gs_options* o) {
   o->beta1 = 0.0;
   o->beta2 = 0.0;
   o->h0 = 0.0;
-  o->tape_capacity = 65536;
+  o->tape_capacity = 1000000;
 }
 
 int gs_dims(int32_t system, int32_t* d, int32_t* p) {
@@ -203,14 +211,13 @@ int gs_dims(int32_t system, int32_t* d, int32_t* p) {
 size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
                           double steps_hint) {
   (void)K;
-  (void)opt;
   int32_t d, p;
   if (dims_of(system, &d, &p) || N < 0) return 0;
   Layout L = layout(N);
   if (!for_vjp) return L.total_fixed;
   if (!(steps_hint > 0.0)) steps_hint = 1.0;
   const double chunks = double(N) * (std::ceil(steps_hint / gs::kChunk) + 1.0) + 1.0;
-  return L.total_fixed + size_t(chunks) * size_t(chunk_bytes(d));
+  return L.total_fixed + size_t(chunks) * size_t(chunk_bytes(d, opt ? opt->precision : GS_FP64));
 }
 
 int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
@@ -235,7 +242,7 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     pb.queue = static_cast<unsigned int*>(workspace);
   }
   if (opt->record_tape) {
-    rc = set_tape(pb, d, N, workspace, workspace_bytes);
+    rc = set_tape(pb, d, opt->precision, opt->tape_capacity, N, workspace, workspace_bytes);
     if (rc) return rc;
     pb.record = 1;
   }
@@ -264,7 +271,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   gs::Problem pb = make_problem(N, y0, params, t0, t1, rtol, atol, K, saveat, opt);
   pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
-  rc = set_tape(pb, d, N, workspace, workspace_bytes);
+  rc = set_tape(pb, d, opt->precision, opt->tape_capacity, N, workspace, workspace_bytes);
   if (rc) return rc;
   pb.queue = static_cast<unsigned int*>(workspace);
   pb.dLdy = dLdy; pb.dLdy0 = dLdy0; pb.dLdp = dLdparams;

@@ -54,6 +54,7 @@ struct Tape {
   unsigned long long* pool_next;
   int32_t* head;   // [N] last chunk of each trajectory (-1: none)
   int32_t* n_rec;  // [N] accepted steps recorded (-1: the tape overflowed)
+  int32_t cap;     // most steps recorded per trajectory (more: the tape overflows)
 };
 
 struct Problem {
@@ -150,15 +151,17 @@ struct Traj {
   static constexpr int D = Sys::D, NP = Sys::P, S = Tab::S;
   static constexpr int NPA = NP > 0 ? NP : 1;
   static constexpr int DL = F32 ? D : 1;
-  // slot layout: y[D] as FP64 (PM 0) or hi[D] lo[D] as FP32 (PM 1, 2), padded to a multiple of
-  // 16 bytes, then a 32-byte tail: PM 0, 1: t, tc, h, flag (FP64); PM 2: th, tl, h, flag (FP32).
-  // Chunk headers and slots are multiples of 16 bytes, so every slot, state and tail is 16-byte
-  // aligned for the vector loads and stores below.
-  static constexpr int kTailOff = (8 * D + 15) / 16 * 16;
-  static constexpr int kSlotBytes = kTailOff + 32;
+  // slot layout: y[D] as FP64 (PM 0) or its FP32 high part (PM 1, 2; the reverse pass recomputes
+  // the stages from the high part alone, as the forward attempt does), padded to a multiple of 16
+  // bytes, then the tail: PM 0, 1: t, tc, h, flag (FP64, 32 bytes); PM 2: th, tl, h, flag (FP32,
+  // 16 bytes). Chunk headers and slots are multiples of 16 bytes, so every slot, state and tail is
+  // 16-byte aligned for the vector loads and stores below.
+  static constexpr int kStateBytes = (F32 ? 4 : 8) * D;
+  static constexpr int kTailOff = (kStateBytes + 15) / 16 * 16;
+  static constexpr int kSlotBytes = kTailOff + (DF ? 16 : 32);
   static_assert(kTailOff % 16 == 0 && kSlotBytes % 16 == 0 && kChunkHeader % 16 == 0,
                 "tape slots must stay 16-byte aligned");
-  static_assert(8 * D <= kTailOff, "state part of a slot overlaps its tail");
+  static_assert(kStateBytes <= kTailOff, "state part of a slot overlaps its tail");
 
   T y[D];     // state (FP64) / high part (FP32), with its sensitivities when MT > 0
   R ylo[DL];  // low part (FP32)
@@ -274,6 +277,43 @@ struct Traj {
     return hh;
   }
 
+  // PM 2: the same starting-step heuristic with FP32 norms, ratio and power, so that starting a
+  // trajectory issues no FP64 arithmetic beyond splitting its inputs (on GB300 an FP64 instruction
+  // costs 64 FP32 ones, and the lanes of a warp wait while one of them starts its trajectory).
+  // (th, tl) must hold t0.
+  __device__ float initial_step_f() {
+    float sc[D];
+    float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const float yi = val(y[i]);
+      sc[i] = atolf + rtolf * fabsf(yi);
+      const float r0 = yi / sc[i];
+      d0 += r0 * r0;
+      const float r1 = val(k1[i]) / sc[i];
+      d1 += r1 * r1;
+    }
+    d0 = sqrtf(d0 / D);
+    d1 = sqrtf(d1 / D);
+    const float span = float(t1 - t0);
+    float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * (d0 / d1);
+    h0 = fminf(h0, span);
+    T y1[D], f1[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) y1[i] = y[i] + (ylo[i] + h0 * k1[i]);
+    Sys::f((th + tl) + h0, y1, p, f1);
+    float d2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      const float r = (val(f1[i]) - val(k1[i])) / sc[i];
+      d2 += r * r;
+    }
+    d2 = sqrtf(d2 / D) / h0;
+    const float dm = fmaxf(d1, d2);
+    const float h1 = (dm <= 1e-15f) ? fmaxf(h0 * 1e-3f, 1e-6f) : exp2f(log2f(0.01f / dm) / float(Tab::ORDER + 1));
+    return fminf(fminf(100.0f * h0, h1), span);
+  }
+
   __device__ void init(const Problem& pb, long long traj) {
     n = traj;
     status = 0; nacc = 0; nrej = 0; kk = 0;
@@ -343,11 +383,13 @@ struct Traj {
     lerr_prev = 0.0f;
     atolf = float(pb.atol);
     rtolf = float(pb.rtol);
-    h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step(pb);
     if constexpr (DF) {
       split_df(t0, th, tl);
       split_df(t1, t1h, t1l);
-      hf = float(h);
+      hf = pb.h0 > 0.0 ? float(pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step_f();
+      h = double(hf);
+    } else {
+      h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step(pb);
     }
   }
 
@@ -413,6 +455,7 @@ struct Traj {
     if constexpr (MT == 0) {  // the tape is recorded by the solve without sensitivities
     const int a = nacc - 1;  // index of the step just accepted
     if (!rec_ok) return;
+    if (a >= pb.tape.cap) { rec_ok = false; return; }
     const int o = a % kChunk;
     if (o == 0) {
       const unsigned long long idx = atomicAdd(pb.tape.pool_next, 1ULL);
@@ -424,18 +467,19 @@ struct Traj {
     unsigned char* slot = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader +
                           (long long)o * kSlotBytes;
     if constexpr (F32) {
-      // 16-byte stores: slots start 16-byte aligned (16-byte header, 8 D + 32 bytes per slot)
-      float v[2 * D];
-#pragma unroll
-      for (int i = 0; i < D; i++) { v[i] = y[i]; v[D + i] = ylo[i]; }
-      if constexpr ((2 * D) % 4 == 0) {
+      // vector stores: slots start 16-byte aligned (16-byte header, slots of multiples of 16 bytes)
+      if constexpr (D % 4 == 0) {
         float4* f4 = reinterpret_cast<float4*>(slot);
 #pragma unroll
-        for (int q = 0; q < (2 * D) / 4; q++) f4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      } else {
+        for (int q = 0; q < D / 4; q++) f4[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+      } else if constexpr (D % 2 == 0) {
         float2* f2 = reinterpret_cast<float2*>(slot);
 #pragma unroll
-        for (int q = 0; q < D; q++) f2[q] = make_float2(v[2 * q], v[2 * q + 1]);
+        for (int q = 0; q < D / 2; q++) f2[q] = make_float2(y[2 * q], y[2 * q + 1]);
+      } else {
+        float* f = reinterpret_cast<float*>(slot);
+#pragma unroll
+        for (int i = 0; i < D; i++) f[i] = y[i];
       }
     } else {
       double* f = reinterpret_cast<double*>(slot);

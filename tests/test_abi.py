@@ -5,11 +5,13 @@ import os
 import re
 
 import pytest
+import torch
 
-from paper_2609_28458_gb300 import _abi
+from paper_2609_28458_gb300 import _abi, api
 from paper_2609_28458_gb300 import build as gsbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sysid_name = {v: k for k, v in _abi.SYSTEMS.items()}
 
 
 @pytest.fixture(scope="module")
@@ -71,10 +73,16 @@ def test_workspace_sizes(lib):
     small = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 0, 0.0)
     big = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 1, 500.0)
     assert small >= 256 and big > small
-    # a tape chunk holds 32 slots of (8 d rounded up to 16, + 32) bytes behind a 16-byte header
+    # a tape chunk holds 32 slots behind a 16-byte header; a slot is the state (8 d bytes in FP64,
+    # 4 d for the FP32 high part) rounded up to 16, then 32 bytes of times (16 in the FP32-pair mode)
     assert (big - small) == (1000 * (16 + 1) + 1) * (16 + 32 * (48 + 32))
-    for sysid, d in ((2, 9), (3, 3)):
-        a = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 0, 0.0)
-        b = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 1, 500.0)
-        slot = (8 * d + 15) // 16 * 16 + 32
-        assert slot % 16 == 0 and (b - a) == (1000 * (16 + 1) + 1) * (16 + 32 * slot)
+    for prec, word, tail in (("fp64", 8, 32), ("fp32", 4, 32), ("fp32df", 4, 16)):
+        o = _abi.options(precision=prec)
+        for sysid, d in ((1, 6), (2, 9), (3, 3)):
+            a = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 0, 0.0)
+            b = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 1, 500.0)
+            slot = (word * d + 15) // 16 * 16 + tail
+            assert slot % 16 == 0 and (b - a) == (1000 * (16 + 1) + 1) * (16 + 32 * slot)
+            # the binding's exact sizing uses the same chunk size
+            na = torch.full((1000,), 500, dtype=torch.int32)
+            assert api.tape_bytes(sysid_name[sysid], 1000, n_accept=na, precision=prec) == a + (1000 * 16 + 1) * (16 + 32 * slot)

@@ -172,6 +172,32 @@ def test_reuse_tape_matches_rerun():
         assert torch.equal(s["y"], b["y"])
 
 
+def test_tape_capacity_limits_recorded_steps():
+    """opt.tape_capacity: trajectories with more accepted steps than the capacity get
+    GS_ST_TAPE_OVERFLOW and NaN gradients; the others are unchanged (same step sequence, same tape)."""
+    ensure_built()
+    e = W.mw(n=256, seed=57, t1=1000.0, rtol=1e-8)
+    e.t1 = np.random.default_rng(5).uniform(50.0, 1000.0, e.n)
+    e.saveat = np.stack([e.t1], axis=1)
+    dev = torch.device("cuda")
+    y0 = torch.as_tensor(e.y0, device=dev)
+    w = torch.as_tensor(np.random.default_rng(6).normal(size=(e.n, 1, 6)), device=dev)
+    for prec in ("fp64", "fp32df"):
+        full = api.vjp("mw", y0, e.params, e.t0, e.t1, e.saveat, e.rtol, e.atol, w, precision=prec)
+        nacc = full["n_accept"].cpu().numpy()
+        cap = int(np.median(nacc))
+        lim = api.vjp("mw", y0, e.params, e.t0, e.t1, e.saveat, e.rtol, e.atol, w, precision=prec, tape_capacity=cap)
+        torch.cuda.synchronize()
+        st = lim["status"].cpu().numpy()
+        over = (st & _abi.ST_TAPE_OVERFLOW) != 0
+        assert np.array_equal(over, nacc > cap) and over.any() and (~over).any()
+        g, gf = lim["dLdy0"].cpu().numpy(), full["dLdy0"].cpu().numpy()
+        assert np.all(np.isnan(g[over])) and np.array_equal(g[~over], gf[~over])
+        assert np.array_equal(lim["dLdparams"].cpu().numpy()[~over], full["dLdparams"].cpu().numpy()[~over])
+        # the forward solution itself is not affected by the tape
+        assert torch.equal(lim["y"], full["y"])
+
+
 def test_autograd_function():
     ensure_built()
     e = W.mw(n=128, seed=54, t1=1000.0)
