@@ -177,3 +177,16 @@ def grad(system, y0, params, t0, t1, saveat, w, rtol=0.0, atol=0.0, method="tsit
                    ctypes.c_int(per_traj), _p(w), _p(y), _p(gy0), _p(gp), _p(st), _p(na), _p(nr), _p(tape),
                    ctypes.c_int(tcap), _p(ntape), ctypes.c_int(nthreads))
     return dict(y=y, dLdy0=gy0, dLdparams=gp[:, :np_], status=st, n_accept=na, n_reject=nr)
+
+
+def sens(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", nthreads=0, **kw):
+    """Solution and full forward-sensitivity matrix S [N, K, d, d + p]: derivatives of y(t_k) with
+    respect to (y0, theta) along the adaptive step sequence (Eq. sens, Eq. stage-sens)."""
+    d, np_, N, y0, params, t0, t1, saveat, per_traj, K = _prep(system, y0, params, t0, t1, saveat)
+    o = opts(method, **kw)
+    y = np.empty((N, K, d)); S = np.empty((N, K, d, d + np_))
+    st = np.zeros(N, np.int32); na = np.zeros(N, np.int32); nr = np.zeros(N, np.int32)
+    lib().orc_sens(_sys(system), ctypes.byref(o), ctypes.c_long(N), _p(y0), _p(params), _p(t0), _p(t1),
+                   ctypes.c_double(rtol), ctypes.c_double(atol), ctypes.c_int(K), _p(saveat), ctypes.c_int(per_traj),
+                   _p(y), _p(S), _p(st), _p(na), _p(nr), ctypes.c_int(nthreads))
+    return dict(y=y, S=S, status=st, n_accept=na, n_reject=nr)

@@ -351,6 +351,27 @@ void grad_one(int sys, const Opts& o, const double* y0, const double* p, double 
   for (int q = 0; q < K * d; q++) yout[q] = out[q].v;
 }
 
+// The full forward-sensitivity matrix S[k][i][m] = d y_i(t_k) / d x_m, x = (y0, theta), on
+// dual numbers of width M = d + p (Eq. sens, Eq. stage-sens), along the adaptive step sequence.
+template <int M>
+void sens_one(int sys, const Opts& o, const double* y0, const double* p, double t0, double t1, double rtol,
+              double atol, int K, const double* save, double* yout, double* S, int* status, int* nacc,
+              int* nrej) {
+  typedef Dual<double, M> D;
+  int d, np;
+  dims(sys, &d, &np);
+  D yd[9], pd[4];
+  for (int i = 0; i < d; i++) { yd[i].v = y0[i]; yd[i].d[i] = 1.0; }
+  for (int q = 0; q < np; q++) { pd[q].v = p[q]; pd[q].d[d + q] = 1.0; }
+  std::vector<D> out(K * d > 0 ? K * d : 1);
+  integrate<D>(sys, o, yd, pd, t0, t1, rtol, atol, K, save, out.data(), status, nacc, nrej, nullptr, 0,
+               nullptr, nullptr, 0);
+  for (int q = 0; q < K * d; q++) {
+    yout[q] = out[q].v;
+    for (int m = 0; m < M; m++) S[q * M + m] = out[q].d[m];
+  }
+}
+
 }  // namespace orc
 
 using namespace orc;
@@ -486,6 +507,36 @@ int orc_grad(int sys, const orc_opts* opt, long N, const double* y0, const doubl
       case 9: grad_one<9>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, ww, yo, g1, g2, status + n, nacc + n, nrej + n, tp, nt); break;
       case 10: grad_one<10>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, ww, yo, g1, g2, status + n, nacc + n, nrej + n, tp, nt); break;
       case 12: grad_one<12>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, ww, yo, g1, g2, status + n, nacc + n, nrej + n, tp, nt); break;
+      default: status[n] = -1;
+    }
+  }
+  return 0;
+}
+
+// Solution and full sensitivity matrix S[N, K, d, d + p] (derivatives with respect to y0, then theta).
+int orc_sens(int sys, const orc_opts* opt, long N, const double* y0, const double* params, const double* t0,
+             const double* t1, double rtol, double atol, int K, const double* saveat, int per_traj, double* yout,
+             double* S, int* status, int* nacc, int* nrej, int nthreads) {
+  int d, np;
+  dims(sys, &d, &np);
+  Opts o = to_opts(opt);
+  int M = d + np;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+  for (long n = 0; n < N; n++) {
+    const double* sv = per_traj ? saveat + n * K : saveat;
+    const double* yy = y0 + n * d;
+    const double* pp = np ? params + n * np : nullptr;
+    double* yo = yout + n * K * d;
+    double* Sn = S + n * (long)K * d * M;
+    switch (M) {
+      case 6: sens_one<6>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, yo, Sn, status + n, nacc + n, nrej + n); break;
+      case 7: sens_one<7>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, yo, Sn, status + n, nacc + n, nrej + n); break;
+      case 9: sens_one<9>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, yo, Sn, status + n, nacc + n, nrej + n); break;
+      case 10: sens_one<10>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, yo, Sn, status + n, nacc + n, nrej + n); break;
+      case 12: sens_one<12>(sys, o, yy, pp, t0[n], t1[n], rtol, atol, K, sv, yo, Sn, status + n, nacc + n, nrej + n); break;
       default: status[n] = -1;
     }
   }
