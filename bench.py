@@ -509,6 +509,73 @@ def run_workload(args):
                       "reference": "FP64 Verner 7 at rtol 1e-12 on a %d-member sample" % ns, "rows": out}), flush=True)
 
 
+def run_flat(args):
+    """Dark-energy distances for a population of cosmologies (Sec. 4.2, the two costs of its table):
+    the integration for a supplied amplitude, and the full cost from (lambda, Om) including the
+    Newton solve for the flat amplitude a0 (Eq. de-flat) with da0/dOm and dy/dOm (Eq. de-ift). One
+    JSON line with a row per ensemble size; accuracy on a sample against FP64 Verner 7 at rtol 1e-12
+    with the same flatness solve."""
+    import torch
+
+    from paper_2609_28458_gb300 import api
+    from paper_2609_28458_gb300 import build as gsbuild
+    from paper_2609_28458_gb300 import metrics as M
+    from paper_2609_28458_gb300 import workloads as W
+
+    gsbuild.build()
+    dev = torch.device("cuda")
+    rtol, gtol = 1e-4, 1e-5
+
+    def timeit(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    rows = []
+    for n in (10_000, 100_000, 1_000_000):
+        e = W.quintessence(n=n, seed=3000, rtol=rtol)
+        y0 = torch.as_tensor(e.y0, device=dev)
+        t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
+        start = torch.as_tensor(e.params, device=dev)          # a0 = 1 - Om - Or: the paper's Newton start
+        kw = dict(method="tsit5", precision="fp32df")
+        fl = api.solve_flat(y0, start, t0, t1, sv, rtol, 1e-3 * rtol, gtol=gtol, **kw)
+        flat_params = fl["params"].clone()
+        sup_ms = timeit(lambda: api.solve("quintessence", y0, flat_params, t0, t1, sv, rtol, 1e-3 * rtol,
+                                          kernel="persistent", **kw))
+        sol_ms = timeit(lambda: api.solve_flat(y0, start, t0, t1, sv, rtol, 1e-3 * rtol, gtol=gtol, **kw))
+        ns = min(n, 16384)
+        idx = torch.as_tensor(np.sort(np.random.default_rng(5).choice(n, ns, replace=False)), device=dev)
+        ref = api.solve_flat(y0[idx], start[idx], t0[idx], t1[idx], sv, 1e-12, 1e-14, method="vern7", precision="fp64",
+                             gtol=1e-12, max_newton=12)
+        pg, pr = flat_params[idx].cpu().numpy(), ref["params"].cpu().numpy()
+        dm, dh = M.distances(fl["y"][idx].cpu().numpy(), pg, e.saveat)
+        dmr, dhr = M.distances(ref["y"].cpu().numpy(), pr, e.saveat)
+        err = np.maximum(np.abs(dm - dmr).max(1), np.abs(dh - dhr).max(1))
+        st = fl["status"].cpu().numpy()
+        row = {"n": n, "rtol": rtol, "atol": 1e-3 * rtol, "gtol": gtol, "method": "tsit5", "precision": "fp32df",
+               "a0_supplied_ms": sup_ms, "a0_supplied_us_per_cosmology": 1e3 * sup_ms / n,
+               "a0_solved_ms": sol_ms, "a0_solved_us_per_cosmology": 1e3 * sol_ms / n,
+               "newton_mean": float(fl["n_newton"].double().mean()), "newton_max": int(fl["n_newton"].max()),
+               "unconverged": int(((st & 64) != 0).sum()), "failed": int(((st & 7) != 0).sum()),
+               "p99_distance_err": M.p99(err), "max_distance_err": float(err.max()), "accepted": M.accepted(err, 1e-4),
+               "a0_max_abs_err": float(np.abs(pg[:, 0] - pr[:, 0]).max()),
+               "dydOm_max_rel_err": float((fl["dydOm"][idx] - ref["dydOm"]).abs().max() / ref["dydOm"].abs().max())}
+        rows.append(row)
+        log(json.dumps(row))
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "workload": "quintessence_flat", "budget": 1e-4, "error_measure": "distance (c/H0)",
+                      "reference": "FP64 Verner 7 at rtol 1e-12 with the same flatness solve, on a sample of up to 16384",
+                      "rows": rows}), flush=True)
+
+
 def run_case(args):
     """Small profiling cases of the headline kernels (no JSON line): the seeded MW workload with
     --n orbits at --rtol, solved twice. 'fwd': persistent forward without a tape; 'fwdrev': forward
@@ -553,12 +620,15 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--case", choices=["fwd", "fwdrev"], help="run a small profiling case instead")
     ap.add_argument("--workload", default="mw",
-                    choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "loghalo"])
+                    choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "quintessence_flat",
+                             "loghalo"])
     ap.add_argument("--precision", default="fp32df")
     ap.add_argument("--rtol", type=float, default=1e-8)
     args = ap.parse_args()
     if args.case:
         run_case(args)
+    elif args.workload == "quintessence_flat":
+        run_flat(args)
     elif args.workload != "mw":
         run_workload(args)
     elif args.impl == "reference":

@@ -70,6 +70,8 @@ typedef enum { GS_KERNEL_AUTO = 0, GS_KERNEL_PLAIN = 1, GS_KERNEL_PERSISTENT = 2
 #define GS_ST_EMPTY_INTERVAL 8  /* t1 <= t0: every output is y0, no step taken          */
 #define GS_ST_SAVEAT_OUTSIDE 16 /* an output time outside [t0,t1] or decreasing: NaN there */
 #define GS_ST_TAPE_OVERFLOW 32  /* gs_vjp: the step tape did not fit; gradients NaN     */
+#define GS_ST_NO_CONVERGENCE 64 /* gs_solve_flat: |g| > gtol after max_newton steps, or
+                                   the last output is not at t1 (then outputs NaN)       */
 
 /* Return codes. */
 #define GS_OK 0
@@ -185,6 +187,30 @@ int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, co
            const gs_options* opt, int32_t m, const double* dy0, const double* dparams, double* y_out,
            double* S_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* workspace,
            size_t workspace_bytes, void* cuda_stream);
+
+/* Quintessence cosmologies (system GS_SYS_QUINTESSENCE) with the amplitude a0 fixed by spatial flatness
+ * (Sec. 4.1, Eq. de-flat): Newton's method on g(a0) = E(0)^2 - 1 = 0, each step one gs_jvp integration
+ * to t1 (N = 0, today) carrying S_a0 = dy/da0 and S_Om = dy/dOm; then the derivative along the flat
+ * models (Eq. de-ift): da0/dOm = -(dg/dOm)/(dg/da0) and dy/dOm = S_Om + (da0/dOm) S_a0.
+ *  params [N,4] (a0, lambda, Om, Or): IN/OUT. params[n,0] is the starting amplitude (the paper starts
+ *    from 1 - Om - Or, exact for a field at rest) and is replaced by the solution.
+ *  saveat [K] (or [N,K]): output e-folds; the last one must equal t1, where g is evaluated.
+ *  y_out [N,K,3]: the solution at the returned a0. dydOm [N,K,3], da0dOm [N], g_out [N] (final E(0)^2 - 1):
+ *    may be NULL.
+ *  status [N]: as gs_jvp, plus GS_ST_NO_CONVERGENCE. n_accept, n_reject [N]: of the last integration.
+ *  n_newton [N]: integrations used until |g| <= gtol (gtol > 0; the residual cannot fall below the
+ *    integration's own error, so gtol is usually of the order of rtol).
+ *  opt: precision GS_FP64 or GS_FP32_DF, as gs_jvp. workspace: gs_flat_workspace_bytes(N, K) bytes,
+ *    256-byte aligned. The call synchronises the stream once per Newton iteration (it reads how many
+ *    cosmologies are still moving), so it cannot be captured into a CUDA graph. */
+int gs_solve_flat(int64_t N, const double* y0, double* params, const double* t0, const double* t1, double rtol,
+                  double atol, int32_t K, const double* saveat, const gs_options* opt, int32_t max_newton,
+                  double gtol, double* y_out, double* dydOm, double* da0dOm, double* g_out, int32_t* status,
+                  int32_t* n_accept, int32_t* n_reject, int32_t* n_newton, void* workspace, size_t workspace_bytes,
+                  void* cuda_stream);
+
+/* Workspace bytes of gs_solve_flat for N cosmologies and K outputs (0 for N < 0 or K < 1). */
+size_t gs_flat_workspace_bytes(int64_t N, int32_t K);
 
 /* Evaluate f (Eq. ivp) and its vector-Jacobian products for M states, as the solver does:
  *  f [M,d] = f(t, y, theta);  gy [M,d] = J_y^T w;  gp [M,p] = J_theta^T w  (gy, gp may be NULL).

@@ -16,11 +16,12 @@ KERNELS = {"auto": 0, "plain": 1, "persistent": 2}
 ORDER = {0: 5, 1: 5, 2: 7}
 
 ST_MAX_STEPS, ST_H_UNDERFLOW, ST_NONFINITE, ST_EMPTY_INTERVAL, ST_SAVEAT_OUTSIDE, ST_TAPE_OVERFLOW = 1, 2, 4, 8, 16, 32
+ST_NO_CONVERGENCE = 64
 ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_WORKSPACE = 0, 1, 2, 3
 
 EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_jvp", "gs_vjp_noalloc", "gs_workspace_bytes",
-           "gs_rhs", "gs_last_error", "gs_version")
+           "gs_solve_flat", "gs_flat_workspace_bytes", "gs_rhs", "gs_last_error", "gs_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -72,6 +73,12 @@ def lib():
     L.gs_vjp_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_int32, _vp, ctypes.POINTER(GsOptions), _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_vjp_noalloc.restype = ctypes.c_int
+    L.gs_solve_flat.argtypes = [ctypes.c_int64, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                _vp, ctypes.POINTER(GsOptions), ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp, _vp,
+                                _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gs_solve_flat.restype = ctypes.c_int
+    L.gs_flat_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    L.gs_flat_workspace_bytes.restype = ctypes.c_size_t
     L.gs_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(GsOptions),
                                      ctypes.c_int32, ctypes.c_double]
     L.gs_workspace_bytes.restype = ctypes.c_size_t

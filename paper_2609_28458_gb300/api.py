@@ -204,6 +204,41 @@ def jvp(system, y0, params, t0, t1, saveat, rtol, atol, dy0=None, dparams=None, 
     return out
 
 
+def solve_flat(y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precision="fp64", max_newton=8, gtol=None,
+               workspace=None, **kw):
+    """Quintessence cosmologies with the amplitude a0 solved from flatness (Sec. 4.1, Eqs. de-flat, de-ift).
+
+    params [N,4] = (a0, lambda, Om, Or); its a0 column is the Newton start (not modified: a copy is
+    solved). saveat must end at t1 (today). gtol defaults to rtol. Returns dict(a0 [N], params [N,4],
+    y [N,K,3], dydOm [N,K,3], da0dOm [N], g [N], status, n_accept, n_reject, n_newton)."""
+    y0 = _dev(y0, None, "y0")
+    dev = y0.device
+    N = y0.shape[0]
+    y0 = y0.reshape(N, 3)
+    prm = _dev(params, dev, "params").reshape(N, 4).clone()
+    t0 = _vec(t0, N, dev, "t0")
+    t1 = _vec(t1, N, dev, "t1")
+    saveat = _dev(saveat, dev, "saveat")
+    per_traj = saveat.dim() == 2
+    K = saveat.shape[-1]
+    opt = _abi.options(method, precision, "persistent", per_traj_saveat=int(per_traj), **kw)
+    out = dict(y=torch.empty((N, K, 3), dtype=torch.float64, device=dev),
+               dydOm=torch.empty((N, K, 3), dtype=torch.float64, device=dev),
+               da0dOm=torch.empty(N, dtype=torch.float64, device=dev), g=torch.empty(N, dtype=torch.float64, device=dev),
+               status=torch.empty(N, dtype=_i32, device=dev), n_accept=torch.empty(N, dtype=_i32, device=dev),
+               n_reject=torch.empty(N, dtype=_i32, device=dev), n_newton=torch.empty(N, dtype=_i32, device=dev))
+    wsb = _ws(dev, _abi.lib().gs_flat_workspace_bytes(N, K), workspace)
+    gtol = float(rtol if gtol is None else gtol)
+    _abi.check(_abi.lib().gs_solve_flat(N, _ptr(y0), _ptr(prm), _ptr(t0), _ptr(t1), float(rtol), float(atol), K,
+                                        _ptr(saveat), ctypes.byref(opt), int(max_newton), gtol, _ptr(out["y"]),
+                                        _ptr(out["dydOm"]), _ptr(out["da0dOm"]), _ptr(out["g"]), _ptr(out["status"]),
+                                        _ptr(out["n_accept"]), _ptr(out["n_reject"]), _ptr(out["n_newton"]), _ptr(wsb),
+                                        wsb.numel(), _stream(dev)))
+    out["params"] = prm
+    out["a0"] = prm[:, 0]
+    return out
+
+
 def rhs(system, t, y, params=None, w=None, precision="fp64"):
     """f(t, y, theta) and, if w is given, J_y^T w and J_theta^T w, evaluated by the device code."""
     y = _dev(y, None, "y")

@@ -43,10 +43,14 @@ struct Adjoint {
   };
 
   // Reverse through stages 0..jmax-1 of a step of length hh whose stage states are Y and whose
-  // stage cotangents are kbar (consumed). Adds to ybar and pacc.
+  // stage cotangents are kbar (consumed). Adds to ybar and pacc: the stages' contributions to
+  // theta-bar are summed in R first and enter the (compensated) accumulator once per step.
   __device__ static void reverse_stages(const T& tr, double tt, double hh, R (*Y)[D], R (*kbar)[D], int jmax,
                                         R* ybar, PAcc& pacc) {
     const R hr = R(hh);
+    R gsum[NPA];
+#pragma unroll
+    for (int q = 0; q < NPA; q++) gsum[q] = R(0);
 #pragma unroll
     for (int j = S - 1; j >= 0; j--) {
       if (j < jmax) {
@@ -55,7 +59,7 @@ struct Adjoint {
 #pragma unroll
         for (int i = 0; i < D; i++) ybar[i] += gy[i];
 #pragma unroll
-        for (int q = 0; q < NP; q++) pacc.add(q, gp[q]);
+        for (int q = 0; q < NP; q++) gsum[q] += gp[q];
 #pragma unroll
         for (int l = 0; l < j; l++) {
           if (Tab::a(j, l) != 0.0) {
@@ -66,6 +70,8 @@ struct Adjoint {
         }
       }
     }
+#pragma unroll
+    for (int q = 0; q < NP; q++) pacc.add(q, gsum[q]);
   }
 
   struct SlotView {
@@ -80,47 +86,57 @@ struct Adjoint {
   __device__ static int32_t prev_chunk(const Problem& pb, int32_t chunk) {
     return int32_t(*reinterpret_cast<const long long*>(pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes));
   }
-  __device__ static SlotView load_times(const unsigned char* s) {
-    SlotView v;
-    if constexpr (DF) {
-      const float4 tail = *reinterpret_cast<const float4*>(s + T::kTailOff);
-      v.th = tail.x; v.tl = tail.y; v.hf = tail.z; v.last = tail.w != 0.0f;
-      v.t = double(v.th) + double(v.tl);
-      v.tc = 0.0;
-      v.h = double(v.hf);
-    } else {
-      const double* tail = reinterpret_cast<const double*>(s + T::kTailOff);
-      v.t = tail[0]; v.tc = tail[1]; v.h = tail[2]; v.last = tail[3] != 0.0;
-    }
-    return v;
-  }
-  // the state at the step's start; in the FP32 modes its high part (the low part is not recorded:
-  // the stages are recomputed from the high part, as in the forward attempt)
-  __device__ static void load_state(const unsigned char* s, T& tr) {
+  // A slot's words as loaded, before any arithmetic consumes them: the next step's slot is fetched
+  // one step ahead into this, so the loads overlap a whole step of arithmetic, and decoded when used.
+  struct Raw {
+    R y[D];          // the state at the step's start (FP32 modes: its high part; the low part is
+                     // not recorded, the stages are recomputed from the high part as in the forward)
+    float4 tf;       // PM 2 tail: th, tl, h, flag
+    double2 t0, t1;  // PM 0, 1 tail: (t, tc), (h, flag)
+  };
+  __device__ static void fetch(const unsigned char* s, Raw& r) {
     if constexpr (F32) {
       if constexpr (D % 4 == 0) {
         const float4* f4 = reinterpret_cast<const float4*>(s);
 #pragma unroll
         for (int q = 0; q < D / 4; q++) {
           const float4 a = f4[q];
-          tr.y[4 * q] = a.x; tr.y[4 * q + 1] = a.y; tr.y[4 * q + 2] = a.z; tr.y[4 * q + 3] = a.w;
+          r.y[4 * q] = a.x; r.y[4 * q + 1] = a.y; r.y[4 * q + 2] = a.z; r.y[4 * q + 3] = a.w;
         }
       } else if constexpr (D % 2 == 0) {
         const float2* f2 = reinterpret_cast<const float2*>(s);
 #pragma unroll
-        for (int q = 0; q < D / 2; q++) { const float2 a = f2[q]; tr.y[2 * q] = a.x; tr.y[2 * q + 1] = a.y; }
+        for (int q = 0; q < D / 2; q++) { const float2 a = f2[q]; r.y[2 * q] = a.x; r.y[2 * q + 1] = a.y; }
       } else {
         const float* f = reinterpret_cast<const float*>(s);
 #pragma unroll
-        for (int i = 0; i < D; i++) tr.y[i] = f[i];
+        for (int i = 0; i < D; i++) r.y[i] = f[i];
       }
-#pragma unroll
-      for (int i = 0; i < D; i++) tr.ylo[i] = 0.0f;
     } else {
-      const double* f = reinterpret_cast<const double*>(s);
+      const double2* f2 = reinterpret_cast<const double2*>(s);
 #pragma unroll
-      for (int i = 0; i < D; i++) tr.y[i] = f[i];
+      for (int q = 0; q < D / 2; q++) { const double2 a = f2[q]; r.y[2 * q] = a.x; r.y[2 * q + 1] = a.y; }
+      if constexpr (D % 2 == 1) r.y[D - 1] = reinterpret_cast<const double*>(s)[D - 1];
     }
+    if constexpr (DF) {
+      r.tf = *reinterpret_cast<const float4*>(s + T::kTailOff);
+    } else {
+      const double2* t = reinterpret_cast<const double2*>(s + T::kTailOff);
+      r.t0 = t[0];
+      r.t1 = t[1];
+    }
+  }
+  __device__ static SlotView decode(const Raw& r) {
+    SlotView v;
+    if constexpr (DF) {
+      v.th = r.tf.x; v.tl = r.tf.y; v.hf = r.tf.z; v.last = r.tf.w != 0.0f;
+      v.t = double(v.th) + double(v.tl);
+      v.tc = 0.0;
+      v.h = double(v.hf);
+    } else {
+      v.t = r.t0.x; v.tc = r.t0.y; v.h = r.t1.x; v.last = r.t1.y != 0.0;
+    }
+    return v;
   }
 
   // the forward's test for an output inside a step, in the same arithmetic
@@ -155,6 +171,7 @@ struct Adjoint {
   int kk, a;
   int32_t chunk;
   bool done;
+  Raw nraw;  // the slot of step a, then (once step a has started) of step a - 1
 
   __device__ void write_const(const Problem& pb, double v_y, double v_p, bool sum_w, bool only_t0) {
     const long long n = tr.n;
@@ -194,7 +211,10 @@ struct Adjoint {
     kk = pb.K - 1;
     a = nrec - 1;
     chunk = pb.tape.head[n];
-    const SlotView last = load_times(slot_ptr(pb, chunk, a % kChunk));
+#pragma unroll
+    for (int i = 0; i < T::DL; i++) tr.ylo[i] = R(0);
+    fetch(slot_ptr(pb, chunk, a % kChunk), nraw);
+    const SlotView last = decode(nraw);
     // outputs emitted after the final step when the interval closed without a clipped last step
     while (kk >= 0) {
       if (!save_valid(pb, n, kk, tr.t0, tr.t1)) { kk--; continue; }
@@ -211,12 +231,12 @@ struct Adjoint {
     const long long n = tr.n;
     const double t0 = tr.t0, t1 = tr.t1;
     const int o = a % kChunk;
-    const unsigned char* sp = slot_ptr(pb, chunk, o);
-    const SlotView cur = load_times(sp);
-    load_state(sp, tr);
+    const SlotView cur = decode(nraw);
+#pragma unroll
+    for (int i = 0; i < D; i++) tr.y[i] = nraw.y[i];
     const int32_t pchunk = (o == 0 && a > 0) ? prev_chunk(pb, chunk) : chunk;
-    // the times of step a - 1 (valid for a > 0): outputs inside it belong to that step
-    const SlotView prev = a > 0 ? load_times(slot_ptr(pb, pchunk, o == 0 ? kChunk - 1 : o - 1)) : cur;
+    // fetch step a - 1 now; its times are decoded only where an output may belong to it
+    if (a > 0) fetch(slot_ptr(pb, pchunk, o == 0 ? kChunk - 1 : o - 1), nraw);
     Sys::f(tr.stage_time(cur.t), tr.y, tr.p, tr.k1);
     // does an output inside this step use the dense polynomial (which needs the last, FSAL stage)?
     bool dense_here = false;
@@ -224,7 +244,7 @@ struct Adjoint {
       for (int q = kk; q >= 0; q--) {
         if (!save_valid(pb, n, q, t0, t1)) continue;
         const double sq = save_at(pb, n, q);
-        if (sq == t0 || !inside(cur, sq) || (a > 0 && inside(prev, sq))) break;
+        if (sq == t0 || !inside(cur, sq) || (a > 0 && inside(decode(nraw), sq))) break;
         if (!(cur.last && sq == t1)) { dense_here = true; break; }
       }
     }
@@ -246,7 +266,7 @@ struct Adjoint {
       const double sv = save_at(pb, n, kk);
       if (sv == t0) break;
       if (!inside(cur, sv)) break;
-      if (a > 0 && inside(prev, sv)) break;
+      if (a > 0 && inside(decode(nraw), sv)) break;
       R w[D];
 #pragma unroll
       for (int i = 0; i < D; i++) w[i] = R(W[kk * D + i]);

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "gs.h"
+#include "gs_internal.h"
 #include "gs_kernels.cuh"
 
 namespace gs {
@@ -135,6 +136,7 @@ gs::Problem make_problem(int64_t N, const double* y0, const double* params, cons
   gs::Problem pb;
   std::memset(&pb, 0, sizeof(pb));
   pb.N = N;
+  pb.n_work = N;
   pb.K = K;
   pb.per_traj = opt->per_traj_saveat ? 1 : 0;
   pb.y0 = y0; pb.params = params; pb.t0 = t0; pb.t1 = t1; pb.saveat = saveat;
@@ -300,6 +302,19 @@ int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, co
            const double* t1, double rtol, double atol, int32_t K, const double* saveat, const gs_options* opt,
            int32_t m, const double* dy0, const double* dparams, double* y_out, double* S_out, int32_t* status,
            int32_t* n_accept, int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  return gs::jvp_on(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, m, dy0, dparams, y_out, S_out, status,
+                    n_accept, n_reject, workspace, workspace_bytes, cuda_stream, nullptr, N);
+}
+
+}  // extern "C"
+
+namespace gs {
+
+int jvp_on(int32_t system, int64_t N, const double* y0, const double* params, const double* t0, const double* t1,
+           double rtol, double atol, int32_t K, const double* saveat, const gs_options* opt, int32_t m,
+           const double* dy0, const double* dparams, double* y_out, double* S_out, int32_t* status, int32_t* n_accept,
+           int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream, const int32_t* work,
+           long long n_work) {
   int32_t d, p;
   int rc = check_common(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, &d, &p);
   if (rc) return rc;
@@ -316,6 +331,11 @@ int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, co
   pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
   pb.queue = static_cast<unsigned int*>(workspace);
   pb.dy0 = dy0; pb.dp = dparams; pb.S_out = S_out; pb.m_total = m;
+  if (work) {
+    if (n_work < 0 || n_work > N) return fail(GS_ERR_INVALID, "work list of %lld entries for N = %lld", n_work, (long long)N);
+    pb.work = work;
+    pb.n_work = n_work;
+  }
   const int group = opt->method == GS_VERN7 ? 1 : 4;
   gs::LaunchCfg c{opt->method, opt->precision, GS_KERNEL_PERSISTENT, opt->block_size, s};
   for (int32_t off = 0; off < m;) {
@@ -330,6 +350,10 @@ int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, co
   }
   return GS_OK;
 }
+
+}  // namespace gs
+
+extern "C" {
 
 int gs_rhs(int32_t system, int32_t precision, int64_t M, const double* t, const double* y, const double* params,
            const double* w, double* f, double* gy, double* gp, void* cuda_stream) {

@@ -44,8 +44,9 @@ struct Occupancy {
 
 template <template <class> class SysT, class Tab, int PM>
 __global__ void __launch_bounds__(128) k_plain(const Problem pb) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= pb.N) return;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= pb.n_work) return;
+  const long long n = pb.work ? (long long)pb.work[i] : i;
   Traj<SysT, Tab, PM> tr;
   tr.init(pb, n);
   while (!tr.done) tr.attempt(pb);
@@ -68,8 +69,8 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_pe
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const unsigned long long idx = (unsigned long long)base + unsigned(__popc(m & lt_mask));
-        if (idx < (unsigned long long)pb.N) {
-          tr.init(pb, (long long)idx);
+        if (idx < (unsigned long long)pb.n_work) {
+          tr.init(pb, pb.work ? (long long)pb.work[idx] : (long long)idx);
           running = true;
           if (tr.done) { tr.finish(pb); running = false; }
         } else {
@@ -87,8 +88,9 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_pe
 
 template <template <class> class SysT, class Tab, int PM>
 __global__ void __launch_bounds__(128) k_reverse(const Problem pb) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= pb.N) return;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= pb.n_work) return;
+  const long long n = pb.work ? (long long)pb.work[i] : i;
   Adjoint<SysT, Tab, PM> adj;
   adj.init(pb, n);
   while (!adj.done) adj.step(pb);
@@ -111,8 +113,8 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_revers
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const unsigned long long idx = (unsigned long long)base + unsigned(__popc(m & lt_mask));
-        if (idx < (unsigned long long)pb.N) {
-          adj.init(pb, (long long)idx);
+        if (idx < (unsigned long long)pb.n_work) {
+          adj.init(pb, pb.work ? (long long)pb.work[idx] : (long long)idx);
           running = !adj.done;
         } else {
           exhausted = true;
@@ -177,15 +179,16 @@ inline int persistent_grid(K kernel, int block) {
 template <template <class> class SysT, class Tab, int PM>
 cudaError_t launch_forward_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
+  if (pb.n_work <= 0) return cudaSuccess;
   if (c.kernel == 2) {
     auto kern = k_persist<SysT, Tab, PM>;
     long long grid = persistent_grid(kern, block);
-    const long long need = (pb.N + block - 1) / block;
+    const long long need = (pb.n_work + block - 1) / block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
   } else {
-    const long long grid = (pb.N + block - 1) / block;
+    const long long grid = (pb.n_work + block - 1) / block;
     k_plain<SysT, Tab, PM><<<unsigned(grid), block, 0, c.stream>>>(pb);
   }
   return cudaGetLastError();
@@ -194,15 +197,16 @@ cudaError_t launch_forward_t(const Problem& pb, const LaunchCfg& c) {
 template <template <class> class SysT, class Tab, int PM>
 cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
+  if (pb.n_work <= 0) return cudaSuccess;
   if (c.kernel == 2) {
     auto kern = k_reverse_persist<SysT, Tab, PM>;
     long long grid = persistent_grid(kern, block);
-    const long long need = (pb.N + block - 1) / block;
+    const long long need = (pb.n_work + block - 1) / block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
   } else {
-    const long long grid = (pb.N + block - 1) / block;
+    const long long grid = (pb.n_work + block - 1) / block;
     k_reverse<SysT, Tab, PM><<<unsigned(grid), block, 0, c.stream>>>(pb);
   }
   return cudaGetLastError();
@@ -212,9 +216,10 @@ cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
 template <template <class> class SysT, class Tab, int PM, int MT>
 cudaError_t launch_jvp_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
+  if (pb.n_work <= 0) return cudaSuccess;
   auto kern = k_persist<SysT, Tab, PM, MT>;
   long long grid = persistent_grid(kern, block);
-  const long long need = (pb.N + block - 1) / block;
+  const long long need = (pb.n_work + block - 1) / block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   kern<<<unsigned(grid), block, 0, c.stream>>>(pb);

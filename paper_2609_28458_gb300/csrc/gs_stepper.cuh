@@ -59,6 +59,10 @@ struct Tape {
 
 struct Problem {
   long long N;
+  // optional work list: a launch processes trajectories work[0 .. n_work - 1] (indices into the
+  // [N, ...] arrays) and leaves the others untouched; without one, n_work = N and work = null
+  const int32_t* work;
+  long long n_work;
   int32_t K, per_traj;
   const double* y0;
   const double* params;

@@ -86,3 +86,24 @@ def test_workspace_sizes(lib):
             # the binding's exact sizing uses the same chunk size
             na = torch.full((1000,), 500, dtype=torch.int32)
             assert api.tape_bytes(sysid_name[sysid], 1000, n_accept=na, precision=prec) == a + (1000 * 16 + 1) * (16 + 32 * slot)
+
+
+def test_solve_flat_argument_checks(lib):
+    """gs_solve_flat rejects bad arguments on the host, before any launch."""
+    o = _abi.options()
+    fake = ctypes.c_void_p(256)
+    ws_need = lib.gs_flat_workspace_bytes(1000, 8)
+    assert ws_need >= 512 + 1000 * 8 * 3 * 2 * 8 + 1000 * 4 * 2 * 8 + 1000 * 4
+    assert lib.gs_flat_workspace_bytes(10, 0) == 0 and lib.gs_flat_workspace_bytes(-1, 4) == 0
+
+    def call(N=4, K=8, max_newton=8, gtol=1e-8, ws=fake, nbytes=1 << 30, opt=o):
+        return lib.gs_solve_flat(N, fake, fake, fake, fake, 1e-6, 1e-9, K, fake, ctypes.byref(opt) if opt else None,
+                                 max_newton, gtol, fake, None, None, None, fake, fake, fake, fake, ws, nbytes, None)
+
+    assert call(K=0) == _abi.GS_ERR_INVALID
+    assert call(max_newton=0) == _abi.GS_ERR_INVALID
+    assert call(gtol=0.0) == _abi.GS_ERR_INVALID and call(gtol=float("nan")) == _abi.GS_ERR_INVALID
+    assert call(opt=None) == _abi.GS_ERR_INVALID
+    assert call(nbytes=1024) == _abi.GS_ERR_WORKSPACE
+    assert call(ws=ctypes.c_void_p(8)) == _abi.GS_ERR_WORKSPACE
+    assert call(N=0) == _abi.GS_OK
