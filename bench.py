@@ -45,11 +45,17 @@ HEAD_PREC = "fp32df"
 # Algorithmic flops (sqrt, div, log counted as one op each), Tsit5 on the MW system:
 #   f:   ~70 add/mul + 4 sqrt + 1 log + 3 div = 78;  VJP of f: ~2.5 f = 195
 #   forward attempt: 6 f (FSAL) + 2d (nnz A + nnz(b - bhat)) = 2*6*(21+7) + ~40 controller = 880
-#   reverse accepted step: 7 f (stage recompute incl. k1) + 2d nnz A (recompute) + 6 VJP
-#                          + 2d (nnz A + nnz b) (adjoint stage algebra) = 2292
+#   reverse accepted step: the 6 stages the new state depends on (b_7 = 0): 6 f (k1 included)
+#                          + 2d (nnz of A among them + the 5 state updates) = 2*6*(15+5),
+#                          6 VJPs, and the cotangent algebra 2d (15 a_lj + 6 b_j) = 2130
 F_RHS_MW = 78
 F_ATT_FWD = 6 * F_RHS_MW + 2 * 6 * (21 + 7) + 40
-F_STEP_REV = 7 * F_RHS_MW + 2 * 6 * 21 + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (21 + 6)
+F_STEP_REV = 6 * F_RHS_MW + 2 * 6 * (15 + 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
+# DRAM bytes per accepted step of k_reverse_persist (fp32df, MW): ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch on 65,536 orbits (2.783 GB for 53.39M accepted steps), scaled by
+# the accepted steps of a launch. The tape slot is 48 bytes; the rest is chunk headers and outputs.
+# Valid for the kernel as profiled under profiles/mw_fp32df_reverse_k_reverse_persist.md only.
+REV_DRAM_BYTES_PER_STEP = 52.1
 # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25  # nominal GB300 FP64 rate
@@ -295,11 +301,14 @@ def run_gpu(args):
     fk, rk = float(np.mean(t_fwd)), float(np.mean(t_rev))
     if rk >= fk:
         dom, flops, dur = "k_reverse_persist (discrete adjoint, fp32df)", n_acc * F_STEP_REV, rk
+        traffic = REV_DRAM_BYTES_PER_STEP * n_acc
     else:
         dom, flops, dur = "k_persist (forward + tape record, fp32df)", n_att * F_ATT_FWD, fk
+        traffic = None
     achieved = flops / (dur / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / PEAK_FP32_TFLOPS, "traffic": None,
+                "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch, from an ncu capture on 65,536 orbits scaled by accepted steps",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"}
 
     # ---------------- forward-only at the state budget ----------------
