@@ -174,3 +174,65 @@ def loghalo(n=10_000, seed=4000, rtol=3.16e-7):
 def by_name(name, **kw):
     return dict(isochrone=isochrone, mw=mw, precession=precession, quintessence=quintessence,
                 loghalo=loghalo)[name](**kw)
+
+
+# ---------------------------------------------------------------------------------------------
+# Profile-likelihood data (Sec. 4.3, Appendix C): synthetic stand-ins for the DESI DR2 BAO distances
+# and the Pantheon+ supernova magnitudes, which are not available. Shapes only: 7 BAO redshift bins
+# (the first with D_V/r_d alone, the others with correlated D_M/r_d and D_H/r_d), 1701 supernovae
+# with a dense covariance (statistical diagonal plus smooth systematic modes), 64 solver output nodes
+# uniform in ln(1+z) over [0, 3]. The mock data sets are model values at a fiducial cosmology plus
+# correlated Gaussian noise drawn here; the model values themselves come from the caller's solver.
+
+C_KMS = 299792.458                  # speed of light, km/s
+PROFILE_FIDUCIAL = dict(lam=0.8, om=0.31, H0=68.0, orad=9e-5, omega_b=0.02218, M_abs=-19.25)
+
+
+@dataclass
+class ProfileData:
+    z_nodes: np.ndarray       # [64] solver output redshifts (z = 0 first)
+    z_bao: np.ndarray         # [7] BAO bin redshifts
+    bao_z: np.ndarray         # [13] redshift of each BAO data point
+    bao_kind: np.ndarray      # [13] 0 = D_V/r_d, 1 = D_M/r_d, 2 = D_H/r_d
+    bao_frac: np.ndarray      # [13] fractional 1-sigma errors
+    bao_rho: float            # correlation of D_M/r_d and D_H/r_d in one bin
+    z_sn: np.ndarray          # [n_sn] supernova redshifts
+    sn_cov: np.ndarray        # [n_sn, n_sn] magnitude covariance (mag^2)
+    lam_grid: np.ndarray      # [n_lam] profile grid of the slope lambda
+    fiducial: dict
+
+
+def profile_data(seed=5000, n_sn=1701, n_lam=100):
+    rng = np.random.default_rng(seed)
+    z_nodes = quintessence_redshifts(dense=True)
+    z_bao = quintessence_redshifts()
+    bao_z = np.concatenate([[z_bao[0]], np.repeat(z_bao[1:], 2)])
+    bao_kind = np.concatenate([[0], np.tile([1, 2], len(z_bao) - 1)]).astype(np.int32)
+    bao_frac = np.where(bao_kind == 0, 0.010, np.where(bao_kind == 1, 0.015, 0.025))
+    # supernova redshifts: most at low z, a tail to z = 2.26 (Pantheon+-like shape)
+    z_sn = np.concatenate([np.exp(rng.uniform(np.log(0.012), np.log(0.1), n_sn * 35 // 100)),
+                           rng.uniform(0.1, 0.8, n_sn * 55 // 100)])
+    z_sn = np.sort(np.concatenate([z_sn, rng.uniform(0.8, 2.26, n_sn - len(z_sn))]))
+    sig = 0.10 + 0.06 * rng.random(n_sn) + 0.02 * z_sn
+    modes = np.stack([0.02 * np.cos(np.pi * k * np.log1p(z_sn) / np.log1p(2.26) + rng.uniform(0, 2 * np.pi))
+                      for k in range(1, 7)], axis=1)
+    sn_cov = np.diag(sig ** 2) + modes @ modes.T
+    lam_grid = np.linspace(0.0, 1.5, n_lam)
+    return ProfileData(z_nodes, z_bao, bao_z, bao_kind, bao_frac, -0.45, z_sn, sn_cov, lam_grid,
+                       dict(PROFILE_FIDUCIAL))
+
+
+def bao_covariance(data, truth_bao):
+    """Covariance of the 13 BAO points: fractional errors of the fiducial values, D_M-D_H correlated."""
+    s = data.bao_frac * np.abs(truth_bao)
+    C = np.diag(s ** 2)
+    for i in range(1, len(s), 2):
+        C[i, i + 1] = C[i + 1, i] = data.bao_rho * s[i] * s[i + 1]
+    return C
+
+
+def profile_mocks(truth, cov, n_mocks, seed=5001):
+    """n_mocks draws of truth + C^{1/2} eps (C^{1/2} the lower Cholesky factor, eps standard normal)."""
+    rng = np.random.default_rng(seed)
+    L = np.linalg.cholesky(cov)
+    return truth[None, :] + rng.standard_normal((n_mocks, len(truth))) @ L.T
