@@ -212,6 +212,54 @@ int gs_solve_flat(int64_t N, const double* y0, double* params, const double* t0,
 /* Workspace bytes of gs_solve_flat for N cosmologies and K outputs (0 for N < 0 or K < 1). */
 size_t gs_flat_workspace_bytes(int64_t N, int32_t K);
 
+/* Profile-likelihood fits of the quintessence model (Sec. 4.3, Appendix C, Eq. de-gn): many damped
+ * Gauss-Newton minimisations of chi^2 over psi = (Om, H0) at fixed lambda, each on one mock data set.
+ * Every iteration is one gs_solve_flat of all fits at n_nodes output redshifts (the flat model and
+ * dy/dOm along flat models), then one kernel that forms chi^2, J^T r and J^T J and takes the step. */
+typedef struct {
+  int32_t method, precision;  /* of the flatness solves (GS_FP64 or GS_FP32_DF) */
+  double rtol, atol, gtol;    /* their tolerances and the flatness residual */
+  int32_t max_newton;         /* Newton steps per flatness solve (8) */
+  int32_t n_iter;             /* Gauss-Newton iterations (20); chi^2 is recomputed after the last */
+  double mu;                  /* damping of Eq. de-gn (1e-3) */
+  double trust_om, trust_h0;  /* trust region: the step is scaled so |dOm| <= 0.02, |dH0| <= 2 */
+  double start_om, start_h0;  /* starting point (0.30, 70 km/s/Mpc) */
+  double orad, omega_b, omega_nu; /* Omega_r (9e-5); baryon and neutrino densities in r_d */
+  double conv_dchi2, conv_decrement; /* convergence test: |Delta chi^2| < 1e-4, decrement < 1e-6 */
+} gs_profile_options;
+
+void gs_profile_default_options(gs_profile_options* opt);
+
+/* Bytes of the prepared-data buffer (0 for unsupported sizes: 4 <= n_nodes <= 64, n_bao <= 32). */
+size_t gs_profile_prep_bytes(int32_t n_nodes, int32_t n_bao, int32_t n_sn, int32_t n_mocks);
+
+/* One-time preparation of the data (device pointers, row-major):
+ *  z_nodes [n_nodes]: output redshifts, ascending, z_nodes[0] = 0, uniform or not in x = ln(1+z);
+ *    distances at the data redshifts come from a not-a-knot cubic spline in x of ln(D_M/z), ln D_H.
+ *  bao_z, bao_kind [n_bao]: redshift and kind of each BAO point (0 D_V/r_d, 1 D_M/r_d, 2 D_H/r_d);
+ *    L_bao [n_bao x n_bao]: lower Cholesky factor of their covariance; d_bao [n_mocks x n_bao].
+ *  z_sn [n_sn], L_sn [n_sn x n_sn] (lower Cholesky factor), d_sn [n_mocks x n_sn]: supernova
+ *    magnitudes; their absolute magnitude is marginalised (projection orthogonal to L_sn^{-1} 1).
+ * The supernova part is reduced to n_nodes x n_nodes quadratic forms in the spline's node values
+ * (exact: the spline is linear in them), so the fits never touch n_sn again. */
+int gs_profile_prepare(int32_t n_nodes, const double* z_nodes, int32_t n_bao, const double* bao_z,
+                       const int32_t* bao_kind, const double* L_bao, int32_t n_sn, const double* z_sn,
+                       const double* L_sn, int32_t n_mocks, const double* d_bao, const double* d_sn, void* prep,
+                       size_t prep_bytes, void* cuda_stream);
+
+/* Workspace bytes of gs_profile_fit for n_fits fits (0 for unsupported n_nodes). */
+size_t gs_profile_workspace_bytes(int64_t n_fits, int32_t n_nodes);
+
+/* n_fits minimisations: lam [n_fits] the fixed slope, mock [n_fits] the data set of each.
+ * Outputs [n_fits]: om, H0 at the returned parameters, a0 (flat amplitude there), chi2 recomputed
+ * there, decrement = g^T (J^T J)^{-1} g (g = J^T r) there, converged (the test of opt), status
+ * (flatness-solve status bits, or GS_ST_NONFINITE for a mock index outside [0, n_mocks); non-zero
+ * stops the fit with NaN chi2). Dimensions as prepared. */
+int gs_profile_fit(int64_t n_fits, const double* lam, const int32_t* mock, const void* prep, int32_t n_nodes,
+                   int32_t n_bao, int32_t n_sn, int32_t n_mocks, const gs_profile_options* opt, double* om, double* H0,
+                   double* a0, double* chi2, double* decrement, int32_t* converged, int32_t* status, void* workspace,
+                   size_t workspace_bytes, void* cuda_stream);
+
 /* Evaluate f (Eq. ivp) and its vector-Jacobian products for M states, as the solver does:
  *  f [M,d] = f(t, y, theta);  gy [M,d] = J_y^T w;  gp [M,p] = J_theta^T w  (gy, gp may be NULL).
  *  precision selects the FP64 (GS_FP64) or FP32 (the two FP32 modes) instantiation. */

@@ -21,7 +21,9 @@ ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_WORKSPACE = 0, 1, 2, 3
 
 EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_jvp", "gs_vjp_noalloc", "gs_workspace_bytes",
-           "gs_solve_flat", "gs_flat_workspace_bytes", "gs_rhs", "gs_last_error", "gs_version")
+           "gs_solve_flat", "gs_flat_workspace_bytes", "gs_profile_default_options", "gs_profile_prep_bytes",
+           "gs_profile_prepare", "gs_profile_workspace_bytes", "gs_profile_fit", "gs_rhs", "gs_last_error",
+           "gs_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -32,6 +34,15 @@ class GsOptions(ctypes.Structure):
                 ("h0", ctypes.c_double), ("per_traj_saveat", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("record_tape", ctypes.c_int32), ("reuse_tape", ctypes.c_int32), ("tape_capacity", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class GsProfileOptions(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("precision", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("gtol", ctypes.c_double), ("max_newton", ctypes.c_int32),
+                ("n_iter", ctypes.c_int32), ("mu", ctypes.c_double), ("trust_om", ctypes.c_double),
+                ("trust_h0", ctypes.c_double), ("start_om", ctypes.c_double), ("start_h0", ctypes.c_double),
+                ("orad", ctypes.c_double), ("omega_b", ctypes.c_double), ("omega_nu", ctypes.c_double),
+                ("conv_dchi2", ctypes.c_double), ("conv_decrement", ctypes.c_double)]
 
 
 class GsError(RuntimeError):
@@ -79,6 +90,19 @@ def lib():
     L.gs_solve_flat.restype = ctypes.c_int
     L.gs_flat_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
     L.gs_flat_workspace_bytes.restype = ctypes.c_size_t
+    L.gs_profile_default_options.argtypes = [ctypes.POINTER(GsProfileOptions)]
+    L.gs_profile_default_options.restype = None
+    L.gs_profile_prep_bytes.argtypes = [ctypes.c_int32] * 4
+    L.gs_profile_prep_bytes.restype = ctypes.c_size_t
+    L.gs_profile_prepare.argtypes = [ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp,
+                                     ctypes.c_int32, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+    L.gs_profile_prepare.restype = ctypes.c_int
+    L.gs_profile_workspace_bytes.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    L.gs_profile_workspace_bytes.restype = ctypes.c_size_t
+    L.gs_profile_fit.argtypes = [ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                 ctypes.c_int32, ctypes.POINTER(GsProfileOptions), _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                 _vp, ctypes.c_size_t, _vp]
+    L.gs_profile_fit.restype = ctypes.c_int
     L.gs_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(GsOptions),
                                      ctypes.c_int32, ctypes.c_double]
     L.gs_workspace_bytes.restype = ctypes.c_size_t
@@ -114,3 +138,15 @@ def dims(system):
     d, p = ctypes.c_int32(), ctypes.c_int32()
     check(lib().gs_dims(SYSTEMS[system] if isinstance(system, str) else int(system), ctypes.byref(d), ctypes.byref(p)))
     return d.value, p.value
+
+
+def profile_options(method="tsit5", precision="fp64", **kw):
+    o = GsProfileOptions()
+    lib().gs_profile_default_options(ctypes.byref(o))
+    o.method = METHODS[method] if isinstance(method, str) else int(method)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown profile option %s" % k)
+        setattr(o, k, v)
+    return o

@@ -239,6 +239,50 @@ def solve_flat(y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precision
     return out
 
 
+class ProfileData:
+    """Prepared data of the profile-likelihood fits (gs_profile_prepare): node redshifts, BAO points
+    with their covariance's Cholesky factor, supernova magnitudes likewise, all mock data sets."""
+
+    def __init__(self, z_nodes, bao_z, bao_kind, L_bao, z_sn, L_sn, d_bao, d_sn, device=None):
+        dev = torch.device(device or "cuda")
+        t = lambda a: _dev(a, dev, "data")
+        self.device = dev
+        self.z_nodes, self.bao_z, self.L_bao = t(z_nodes), t(bao_z), t(L_bao)
+        self.z_sn, self.L_sn = t(z_sn), t(L_sn)
+        self.d_bao, self.d_sn = t(d_bao).reshape(-1, len(bao_z)), t(d_sn).reshape(-1, len(z_sn))
+        self.bao_kind = torch.as_tensor(bao_kind, dtype=_i32).to(dev).contiguous()
+        self.n_nodes, self.n_bao, self.n_sn = len(z_nodes), len(bao_z), len(z_sn)
+        self.n_mocks = self.d_sn.shape[0]
+        nbytes = _abi.lib().gs_profile_prep_bytes(self.n_nodes, self.n_bao, self.n_sn, self.n_mocks)
+        if not nbytes:
+            raise ValueError("unsupported profile data sizes")
+        self.buf = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+        _abi.check(_abi.lib().gs_profile_prepare(self.n_nodes, _ptr(self.z_nodes), self.n_bao, _ptr(self.bao_z),
+                                                 _ptr(self.bao_kind), _ptr(self.L_bao), self.n_sn, _ptr(self.z_sn),
+                                                 _ptr(self.L_sn), self.n_mocks, _ptr(self.d_bao), _ptr(self.d_sn),
+                                                 _ptr(self.buf), self.buf.numel(), _stream(dev)))
+
+
+def profile_fit(data, lam, mock, workspace=None, **opts):
+    """Gauss-Newton fits (Eq. de-gn) of (Om, H0) at fixed lambda [n] on mock data sets mock [n] of a
+    ProfileData. Returns dict(om, H0, a0, chi2, decrement, converged, status)."""
+    dev = data.device
+    lam = _dev(lam, dev, "lam").reshape(-1)
+    n = lam.shape[0]
+    mock = torch.as_tensor(mock, dtype=_i32).to(dev).reshape(-1).contiguous()
+    o = _abi.profile_options(**opts)
+    out = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in ("om", "H0", "a0", "chi2", "decrement")}
+    out["converged"] = torch.empty(n, dtype=_i32, device=dev)
+    out["status"] = torch.empty(n, dtype=_i32, device=dev)
+    wsb = _ws(dev, _abi.lib().gs_profile_workspace_bytes(n, data.n_nodes), workspace)
+    _abi.check(_abi.lib().gs_profile_fit(n, _ptr(lam), _ptr(mock), _ptr(data.buf), data.n_nodes, data.n_bao,
+                                         data.n_sn, data.n_mocks, ctypes.byref(o), _ptr(out["om"]), _ptr(out["H0"]),
+                                         _ptr(out["a0"]), _ptr(out["chi2"]), _ptr(out["decrement"]),
+                                         _ptr(out["converged"]), _ptr(out["status"]), _ptr(wsb), wsb.numel(),
+                                         _stream(dev)))
+    return out
+
+
 def rhs(system, t, y, params=None, w=None, precision="fp64"):
     """f(t, y, theta) and, if w is given, J_y^T w and J_theta^T w, evaluated by the device code."""
     y = _dev(y, None, "y")
