@@ -735,6 +735,52 @@ def run_profile(args):
                       "prepare_s": prep_s, "rows": rows}), flush=True)
 
 
+def run_mixed(args):
+    """The mixed serving batch (configuration 5): 100 slopes x 100 mocks of profile-likelihood fits
+    (20 Gauss-Newton iterations, flatness solve with sensitivities inside each), 2^18 Milky-Way orbit
+    gradients and 2^17 precession gradients (Verner 7, FP64), as one CUDA graph with the pieces on
+    concurrent streams and SM budgets from the autotuner, against the same pieces run one after
+    another on the whole GPU. Variants: orbits in the FP32-pair mode, and everything in FP64."""
+    import torch
+
+    from paper_2609_28458_gb300 import api, autotune, serving
+    from paper_2609_28458_gb300 import build as gsbuild
+
+    gsbuild.build()
+    rows = []
+    for variant, mw_prec in (("fp32_stages", "fp32df"), ("full_fp64", "fp64")):
+        P = serving.pieces(mw_precision=mw_prec)
+        shares, alone = autotune.share_sms(P, reps=1)
+        seq = 0.0
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for f in P.values():
+            f(0)
+        b.record()
+        torch.cuda.synchronize()
+        seq = a.elapsed_time(b)
+        mb = api.MixedBatch(P, sm_limits=shares)
+        best = float("inf")
+        for _ in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = mb.replay()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        row = {"variant": variant, "sm_limits": shares, "alone_ms": alone, "sequential_ms": seq, "graph_ms": best,
+               "fits_converged_fraction": float((out["fits"]["converged"] == 1).double().mean()),
+               "orbit_failures": int((out["orbits"]["status"] != 0).sum()),
+               "precession_failures": int(((out["precession"]["status"] & 7) != 0).sum()),
+               "throughput": {"fits_per_s": 10_000 / (best / 1e3), "orbit_grads_per_s": (1 << 18) / (best / 1e3),
+                              "precession_grads_per_s": (1 << 17) / (best / 1e3)}}
+        rows.append(row)
+        log(json.dumps(row))
+        del mb, P, out
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "workload": "mixed_serving_batch", "rows": rows}), flush=True)
+
+
 def run_case(args):
     """Small profiling cases of the headline kernels (no JSON line): the seeded MW workload with
     --n orbits at --rtol, solved twice. 'fwd': persistent forward without a tape; 'fwdrev': forward
@@ -780,7 +826,7 @@ def main():
     ap.add_argument("--case", choices=["fwd", "fwdrev"], help="run a small profiling case instead")
     ap.add_argument("--workload", default="mw",
                     choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "quintessence_flat",
-                             "loghalo", "streams", "profile"])
+                             "loghalo", "streams", "profile", "mixed"])
     ap.add_argument("--precision", default="fp32df")
     ap.add_argument("--rtol", type=float, default=1e-8)
     args = ap.parse_args()
@@ -792,6 +838,8 @@ def main():
         run_streams(args)
     elif args.workload == "profile":
         run_profile(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     elif args.workload != "mw":
         run_workload(args)
     elif args.impl == "reference":

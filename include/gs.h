@@ -97,6 +97,13 @@ typedef struct {
                               gs_solve (same inputs and options) instead of re-solving */
   int32_t tape_capacity;   /* max accepted steps recorded per trajectory (1e6); a
                               trajectory with more gets GS_ST_TAPE_OVERFLOW            */
+  int32_t sm_limit;        /* persistent kernels launch at most this many SMs' worth of
+                              resident blocks (0 = every SM), so that kernels launched
+                              concurrently on other streams share the GPU              */
+  int32_t graph_safe;      /* gs_solve_flat / gs_profile_fit: no host synchronisation;
+                              every Newton iteration is launched (max_newton of them)
+                              and work-list lengths stay on the device, so the calls
+                              can be captured into a CUDA graph                        */
   int32_t reserved;
 } gs_options;
 
@@ -201,8 +208,10 @@ int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, co
  *  n_newton [N]: integrations used until |g| <= gtol (gtol > 0; the residual cannot fall below the
  *    integration's own error, so gtol is usually of the order of rtol).
  *  opt: precision GS_FP64 or GS_FP32_DF, as gs_jvp. workspace: gs_flat_workspace_bytes(N, K) bytes,
- *    256-byte aligned. The call synchronises the stream once per Newton iteration (it reads how many
- *    cosmologies are still moving), so it cannot be captured into a CUDA graph. */
+ *    256-byte aligned. By default the call synchronises the stream once per Newton iteration (it
+ *    reads how many cosmologies are still moving and stops when none is); with opt->graph_safe it
+ *    launches all max_newton iterations, the later ones over device-side work lists that may be
+ *    empty, and never synchronises, so it can be captured into a CUDA graph. */
 int gs_solve_flat(int64_t N, const double* y0, double* params, const double* t0, const double* t1, double rtol,
                   double atol, int32_t K, const double* saveat, const gs_options* opt, int32_t max_newton,
                   double gtol, double* y_out, double* dydOm, double* da0dOm, double* g_out, int32_t* status,
@@ -226,6 +235,8 @@ typedef struct {
   double start_om, start_h0;  /* starting point (0.30, 70 km/s/Mpc) */
   double orad, omega_b, omega_nu; /* Omega_r (9e-5); baryon and neutrino densities in r_d */
   double conv_dchi2, conv_decrement; /* convergence test: |Delta chi^2| < 1e-4, decrement < 1e-6 */
+  int32_t graph_safe;         /* flatness solves without host synchronisation (gs_options) */
+  int32_t sm_limit;           /* SM budget of the flatness solves' persistent kernels (gs_options) */
 } gs_profile_options;
 
 void gs_profile_default_options(gs_profile_options* opt);

@@ -33,7 +33,7 @@ class GsOptions(ctypes.Structure):
                 ("alpha_max", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("h0", ctypes.c_double), ("per_traj_saveat", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("record_tape", ctypes.c_int32), ("reuse_tape", ctypes.c_int32), ("tape_capacity", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("sm_limit", ctypes.c_int32), ("graph_safe", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class GsProfileOptions(ctypes.Structure):
@@ -42,7 +42,8 @@ class GsProfileOptions(ctypes.Structure):
                 ("n_iter", ctypes.c_int32), ("mu", ctypes.c_double), ("trust_om", ctypes.c_double),
                 ("trust_h0", ctypes.c_double), ("start_om", ctypes.c_double), ("start_h0", ctypes.c_double),
                 ("orad", ctypes.c_double), ("omega_b", ctypes.c_double), ("omega_nu", ctypes.c_double),
-                ("conv_dchi2", ctypes.c_double), ("conv_decrement", ctypes.c_double)]
+                ("conv_dchi2", ctypes.c_double), ("conv_decrement", ctypes.c_double), ("graph_safe", ctypes.c_int32),
+                ("sm_limit", ctypes.c_int32)]
 
 
 class GsError(RuntimeError):

@@ -393,3 +393,41 @@ class GraphedStep:
     def replay(self):
         self.graph.replay()
         return self.outputs
+
+
+class MixedBatch:
+    """A serving batch of independent pieces (e.g. profile-likelihood fits, orbit gradients and
+    precession solves) issued on one stream each and captured as one CUDA graph, so that they run
+    concurrently; each piece's persistent kernels are held to its SM budget (gs_options.sm_limit).
+
+    pieces: dict name -> callable(sm_limit) that enqueues the piece on the current stream and returns
+    its output tensors. Every piece must use its own workspaces (concurrent pieces must not share
+    scratch) and launch only stream-ordered work (graph-safe flatness solves for the fits). The
+    callables are run once outside capture (library load, workspace allocation), then captured."""
+
+    def __init__(self, pieces, sm_limits=None, device=None):
+        dev = torch.device(device or "cuda")
+        self.device = dev
+        self.sm_limits = dict(sm_limits or {k: 0 for k in pieces})
+        for k, f in pieces.items():
+            f(self.sm_limits[k])
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        s0 = torch.cuda.Stream(dev)
+        side = {k: torch.cuda.Stream(dev) for k in pieces}
+        s0.wait_stream(torch.cuda.current_stream(dev))
+        self.outputs = {}
+        with torch.cuda.stream(s0):
+            with torch.cuda.graph(self.graph, stream=s0):
+                for k, f in pieces.items():
+                    side[k].wait_stream(s0)
+                    with torch.cuda.stream(side[k]):
+                        self.outputs[k] = f(self.sm_limits[k])
+                for st in side.values():
+                    s0.wait_stream(st)
+        torch.cuda.current_stream(dev).wait_stream(s0)
+
+    def replay(self):
+        """Run the whole batch (asynchronously on the current stream's device) and return the outputs."""
+        self.graph.replay()
+        return self.outputs

@@ -99,3 +99,28 @@ def tune(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precisi
                   "tuned_at": t}
     save_cache(cache, cache_path)
     return kernel, block
+
+
+def share_sms(pieces, sm_count=None, reps=2):
+    """SM budgets for the pieces of a MixedBatch: each piece is timed alone on the whole GPU and gets
+    SMs in proportion to its time, so that the concurrent pieces finish together. Returns
+    (dict name -> sm_limit, dict name -> ms alone)."""
+    dev = torch.device("cuda")
+    if sm_count is None:
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alone = {}
+    for k, f in pieces.items():
+        f(0)
+        torch.cuda.synchronize(dev)
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f(0)
+            b.record()
+            torch.cuda.synchronize(dev)
+            best = min(best, a.elapsed_time(b))
+        alone[k] = best
+    total = sum(alone.values())
+    shares = {k: max(1, int(round(sm_count * t / total))) for k, t in alone.items()}
+    return shares, alone

@@ -202,6 +202,8 @@ void gs_default_options(gs_options* o) {
   o->beta2 = 0.0;
   o->h0 = 0.0;
   o->tape_capacity = 1000000;
+  o->sm_limit = 0;
+  o->graph_safe = 0;
 }
 
 int gs_dims(int32_t system, int32_t* d, int32_t* p) {
@@ -252,7 +254,7 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   }
-  gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s};
+  gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s, opt->sm_limit};
   cudaError_t e = forward_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   return GS_OK;
@@ -278,7 +280,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   pb.queue = static_cast<unsigned int*>(workspace);
   pb.dLdy = dLdy; pb.dLdy0 = dLdy0; pb.dLdp = dLdparams;
   const int kernel = opt->kernel == GS_KERNEL_AUTO ? GS_KERNEL_PERSISTENT : opt->kernel;
-  gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s};
+  gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s, opt->sm_limit};
   if (!opt->reuse_tape) {
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -303,7 +305,7 @@ int gs_jvp(int32_t system, int64_t N, const double* y0, const double* params, co
            int32_t m, const double* dy0, const double* dparams, double* y_out, double* S_out, int32_t* status,
            int32_t* n_accept, int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream) {
   return gs::jvp_on(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, m, dy0, dparams, y_out, S_out, status,
-                    n_accept, n_reject, workspace, workspace_bytes, cuda_stream, nullptr, N);
+                    n_accept, n_reject, workspace, workspace_bytes, cuda_stream, nullptr, N, nullptr);
 }
 
 }  // extern "C"
@@ -314,7 +316,7 @@ int jvp_on(int32_t system, int64_t N, const double* y0, const double* params, co
            double rtol, double atol, int32_t K, const double* saveat, const gs_options* opt, int32_t m,
            const double* dy0, const double* dparams, double* y_out, double* S_out, int32_t* status, int32_t* n_accept,
            int32_t* n_reject, void* workspace, size_t workspace_bytes, void* cuda_stream, const int32_t* work,
-           long long n_work) {
+           long long n_work, const unsigned int* n_work_dev) {
   int32_t d, p;
   int rc = check_common(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, &d, &p);
   if (rc) return rc;
@@ -335,9 +337,10 @@ int jvp_on(int32_t system, int64_t N, const double* y0, const double* params, co
     if (n_work < 0 || n_work > N) return fail(GS_ERR_INVALID, "work list of %lld entries for N = %lld", n_work, (long long)N);
     pb.work = work;
     pb.n_work = n_work;
+    pb.n_work_dev = n_work_dev;  // at most n_work entries (checked by the writer of the list)
   }
   const int group = opt->method == GS_VERN7 ? 1 : 4;
-  gs::LaunchCfg c{opt->method, opt->precision, GS_KERNEL_PERSISTENT, opt->block_size, s};
+  gs::LaunchCfg c{opt->method, opt->precision, GS_KERNEL_PERSISTENT, opt->block_size, s, opt->sm_limit};
   for (int32_t off = 0; off < m;) {
     const int32_t left = m - off;
     const int mt = left >= 4 && group >= 4 ? 4 : (left >= 2 && group >= 2 ? 2 : 1);

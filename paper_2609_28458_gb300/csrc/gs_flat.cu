@@ -10,8 +10,9 @@
 //   da0/dOm = -(dg/dOm) / (dg/da0),   dy/dOm = S_Om + (da0/dOm) S_a0   at every output,
 // and takes the Newton step a0 <- a0 - g / (dg/da0) where |g| > gtol. A cosmology stops at the first
 // iteration with |g| <= gtol and keeps that iteration's outputs: k_flat_newton appends the ones that
-// moved to the next iteration's work list, and the next launches integrate only that list (the host
-// reads its length once per iteration and stops when it is empty).
+// moved to the next iteration's work list, and the next launches integrate only that list. The host
+// reads the list's length once per iteration and stops when it is empty; in the graph-safe mode the
+// length stays on the device and every one of the max_newton iterations is launched.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -28,7 +29,7 @@ constexpr int32_t kFailed = GS_ST_MAX_STEPS | GS_ST_H_UNDERFLOW | GS_ST_NONFINIT
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
-// workspace: [0, 256) gs_jvp's work counter, [256, 512) the length of the next work list, then
+// workspace: [0, 256) gs_jvp's work counter, [256, 512) the lengths of the two work lists, then
 // S [N,K,3,2], the directions [N,4,2] and two work lists [N] (this iteration's and the next)
 struct FlatLayout {
   size_t S, dirs, list0, list1, total;
@@ -55,14 +56,17 @@ __global__ void k_flat_dirs(long long N, double* dirs) {
     for (int m = 0; m < kM; m++) dirs[(n * kP + q) * kM + m] = ((q == 0 && m == 0) || (q == 2 && m == 1)) ? 1.0 : 0.0;
 }
 
-// One Newton iteration over the cosmologies work[0 .. n_work - 1] (all when work is null), just
-// integrated; the ones that take a step are appended to next[] (*n_next entries).
-__global__ void k_flat_newton(long long n_work, const int32_t* work, int K, const double* saveat, int per_traj,
-                              const double* t1, double* params, const double* y_out, const double* S, int32_t* status,
-                              int32_t* n_newton, double* dydOm, double* da0dOm, double* g_out, int it, int max_newton,
-                              double gtol, int32_t* next, unsigned int* n_next) {
+// One Newton iteration over the cosmologies work[0 .. n_work - 1] (all when work is null; the
+// length is *n_work_dev when that is set), just integrated; the ones that take a step are appended
+// to next[] (*n_next entries).
+__global__ void k_flat_newton(long long n_work, const unsigned int* n_work_dev, const int32_t* work, int K,
+                              const double* saveat, int per_traj, const double* t1, double* params,
+                              const double* y_out, const double* S, int32_t* status, int32_t* n_newton, double* dydOm,
+                              double* da0dOm, double* g_out, int it, int max_newton, double gtol, int32_t* next,
+                              unsigned int* n_next) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n_work) return;
+  const long long nw = n_work_dev ? (long long)*n_work_dev : n_work;
+  if (i >= nw) return;
   const long long n = work ? (long long)work[i] : i;
   const double nanv = __longlong_as_double(0x7ff8000000000000LL);
   double* th = params + n * kP;
@@ -141,35 +145,45 @@ int gs_solve_flat(int64_t N, const double* y0, double* params, const double* t0,
   if (N > 0x7fffffffLL) return flat_fail(GS_ERR_INVALID, "gs_solve_flat takes at most 2^31 - 1 cosmologies");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
-  unsigned int* n_next = reinterpret_cast<unsigned int*>(ws + 256);
+  unsigned int* counts = reinterpret_cast<unsigned int*>(ws + 256);  // lengths of lists[0], lists[1]
   double* S = reinterpret_cast<double*>(ws + L.S);
   double* dirs = reinterpret_cast<double*>(ws + L.dirs);
   int32_t* lists[2] = {reinterpret_cast<int32_t*>(ws + L.list0), reinterpret_cast<int32_t*>(ws + L.list1)};
   const int per_traj = opt->per_traj_saveat ? 1 : 0;
+  const bool sync_free = opt->graph_safe != 0;
   const int block = 256;
   k_flat_dirs<<<unsigned((N + block - 1) / block), block, 0, s>>>((long long)N, dirs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return flat_fail(GS_ERR_CUDA, cudaGetErrorString(e));
-  const int32_t* work = nullptr;  // the first iteration integrates every cosmology
+  // the first iteration integrates every cosmology; later ones the list the previous one built, whose
+  // length the host reads back (or, graph-safe, the kernels read on the device)
+  const int32_t* work = nullptr;
   long long n_work = N;
+  const unsigned int* n_work_dev = nullptr;
   for (int it = 0; it < max_newton && n_work > 0; it++) {
     const int rc = gs::jvp_on(GS_SYS_QUINTESSENCE, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, kM, nullptr, dirs,
-                              y_out, S, status, n_accept, n_reject, workspace, 256, cuda_stream, work, n_work);
+                              y_out, S, status, n_accept, n_reject, workspace, 256, cuda_stream, work, n_work,
+                              n_work_dev);
     if (rc) return rc;
     int32_t* next = lists[it & 1];
+    unsigned int* n_next = counts + (it & 1);
     e = cudaMemsetAsync(n_next, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return flat_fail(GS_ERR_CUDA, cudaGetErrorString(e));
     k_flat_newton<<<unsigned((n_work + block - 1) / block), block, 0, s>>>(
-        n_work, work, K, saveat, per_traj, t1, params, y_out, S, status, n_newton, dydOm, da0dOm, g_out, it, max_newton,
-        gtol, next, n_next);
+        n_work, n_work_dev, work, K, saveat, per_traj, t1, params, y_out, S, status, n_newton, dydOm, da0dOm, g_out, it,
+        max_newton, gtol, next, n_next);
     e = cudaGetLastError();
     if (e != cudaSuccess) return flat_fail(GS_ERR_CUDA, cudaGetErrorString(e));
-    unsigned int left = 0;
-    e = cudaMemcpyAsync(&left, n_next, sizeof left, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return flat_fail(GS_ERR_CUDA, cudaGetErrorString(e));
     work = next;
-    n_work = (long long)left;
+    if (sync_free) {
+      n_work_dev = n_next;  // n_work stays N: the grid is sized for the longest possible list
+    } else {
+      unsigned int left = 0;
+      e = cudaMemcpyAsync(&left, n_next, sizeof left, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return flat_fail(GS_ERR_CUDA, cudaGetErrorString(e));
+      n_work = (long long)left;
+    }
   }
   return GS_OK;
 }

@@ -22,6 +22,7 @@ namespace gs {
 struct LaunchCfg {
   int method, precision, kernel, block;
   cudaStream_t stream;
+  int sm_limit;  // persistent kernels: at most this many SMs' worth of resident blocks (0: all SMs)
 };
 
 // Resident 128-thread blocks per SM requested from the register allocator (__launch_bounds__), for
@@ -56,6 +57,7 @@ __global__ void __launch_bounds__(128) k_plain(const Problem pb) {
 template <template <class> class SysT, class Tab, int PM, int MT = 0>
 __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_persist(const Problem pb) {
   Traj<SysT, Tab, PM, MT> tr;
+  const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
   bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_pe
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const unsigned long long idx = (unsigned long long)base + unsigned(__popc(m & lt_mask));
-        if (idx < (unsigned long long)pb.n_work) {
+        if (idx < n_work) {
           tr.init(pb, pb.work ? (long long)pb.work[idx] : (long long)idx);
           running = true;
           if (tr.done) { tr.finish(pb); running = false; }
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(128) k_reverse(const Problem pb) {
 template <template <class> class SysT, class Tab, int PM>
 __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_reverse_persist(const Problem pb) {
   Adjoint<SysT, Tab, PM> adj;
+  const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
   bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_revers
       base = __shfl_sync(0xffffffffu, base, leader);
       if (need) {
         const unsigned long long idx = (unsigned long long)base + unsigned(__popc(m & lt_mask));
-        if (idx < (unsigned long long)pb.n_work) {
+        if (idx < n_work) {
           adj.init(pb, pb.work ? (long long)pb.work[idx] : (long long)idx);
           running = !adj.done;
         } else {
@@ -169,11 +172,12 @@ inline int sm_count() {
 }
 
 template <class K>
-inline int persistent_grid(K kernel, int block) {
+inline int persistent_grid(K kernel, int block, int sm_limit) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
   if (per_sm < 1) per_sm = 1;
-  return per_sm * sm_count();
+  const int sms = (sm_limit > 0 && sm_limit < sm_count()) ? sm_limit : sm_count();
+  return per_sm * sms;
 }
 
 template <template <class> class SysT, class Tab, int PM>
@@ -182,7 +186,7 @@ cudaError_t launch_forward_t(const Problem& pb, const LaunchCfg& c) {
   if (pb.n_work <= 0) return cudaSuccess;
   if (c.kernel == 2) {
     auto kern = k_persist<SysT, Tab, PM>;
-    long long grid = persistent_grid(kern, block);
+    long long grid = persistent_grid(kern, block, c.sm_limit);
     const long long need = (pb.n_work + block - 1) / block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -200,7 +204,7 @@ cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
   if (pb.n_work <= 0) return cudaSuccess;
   if (c.kernel == 2) {
     auto kern = k_reverse_persist<SysT, Tab, PM>;
-    long long grid = persistent_grid(kern, block);
+    long long grid = persistent_grid(kern, block, c.sm_limit);
     const long long need = (pb.n_work + block - 1) / block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -218,7 +222,7 @@ cudaError_t launch_jvp_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
   if (pb.n_work <= 0) return cudaSuccess;
   auto kern = k_persist<SysT, Tab, PM, MT>;
-  long long grid = persistent_grid(kern, block);
+  long long grid = persistent_grid(kern, block, c.sm_limit);
   const long long need = (pb.n_work + block - 1) / block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;

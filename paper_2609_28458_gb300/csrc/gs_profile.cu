@@ -480,6 +480,8 @@ void gs_profile_default_options(gs_profile_options* o) {
   o->omega_nu = 0.00064;
   o->conv_dchi2 = 1e-4;
   o->conv_decrement = 1e-6;
+  o->graph_safe = 0;
+  o->sm_limit = 0;
 }
 
 size_t gs_profile_prep_bytes(int32_t n_nodes, int32_t n_bao, int32_t n_sn, int32_t n_mocks) {
@@ -595,6 +597,8 @@ int gs_profile_fit(int64_t n_fits, const double* lam, const int32_t* mock, const
   fo.method = opt->method;
   fo.precision = opt->precision;
   fo.kernel = GS_KERNEL_PERSISTENT;
+  fo.graph_safe = opt->graph_safe;
+  fo.sm_limit = opt->sm_limit;
   for (int it = 0; it <= opt->n_iter; it++) {
     // the flat model at the current (lambda, Om), Newton on a0 from the moved amplitude; the
     // solver's params hold the flat a0 afterwards

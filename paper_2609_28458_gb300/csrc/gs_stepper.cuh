@@ -60,9 +60,12 @@ struct Tape {
 struct Problem {
   long long N;
   // optional work list: a launch processes trajectories work[0 .. n_work - 1] (indices into the
-  // [N, ...] arrays) and leaves the others untouched; without one, n_work = N and work = null
+  // [N, ...] arrays) and leaves the others untouched; without one, n_work = N and work = null. The
+  // persistent kernels take the length from *n_work_dev instead when it is set (n_work is then
+  // the largest possible length, used to size the grid).
   const int32_t* work;
   long long n_work;
+  const unsigned int* n_work_dev;
   int32_t K, per_traj;
   const double* y0;
   const double* params;
