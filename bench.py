@@ -427,15 +427,18 @@ def run_workload(args):
     if name == "isochrone":
         e = W.isochrone(n=4096, seed=0)
         rows = [("fp64", "plain", "tsit5", 1e-10, 1e-12, False), ("fp64", "persistent", "tsit5", 1e-10, 1e-12, False),
-                ("fp64", "persistent", "tsit5", 1e-10, 1e-12, True)]
+                ("fp64", "persistent", "tsit5", 1e-10, 1e-12, True), ("df64", "plain", "tsit5", 1e-10, 1e-12, False),
+                ("df64", "persistent", "tsit5", 1e-10, 1e-12, True)]
         budget, meas = 1e-4, "orbit"
     elif name in ("precession", "precession_paper"):
         # "precession": from the 20 Hz gravitational-wave frequency to v = 0.3; "precession_paper": the
         # paper's own interval r = 100 M -> 10 M (Sec. 5)
         e = W.precession(n=1_000_000, seed=2000, paper_interval=(name == "precession_paper"))
         rows = [("fp64", "plain", "vern7", 3.16e-9, 3.16e-9, True), ("fp64", "persistent", "vern7", 3.16e-9, 3.16e-9, True),
+                ("df64", "persistent", "vern7", 3.16e-9, 3.16e-9, True),
                 ("fp64", "plain", "tsit5", 5.62e-10, 5.62e-10, False),
-                ("fp64", "persistent", "tsit5", 5.62e-10, 5.62e-10, False)]
+                ("fp64", "persistent", "tsit5", 5.62e-10, 5.62e-10, False),
+                ("df64", "persistent", "tsit5", 5.62e-10, 5.62e-10, False)]
         budget, meas = 2e-7, "angle"
     elif name == "quintessence":
         e = W.quintessence(n=10_000, seed=3000)

@@ -54,8 +54,13 @@ typedef enum { GS_TSIT5 = 0, GS_DOPRI5 = 1, GS_VERN7 = 2 } gs_method;
  *   controller in FP64.
  * GS_FP32_DF: as GS_FP32_STAGES, but the time is an unevaluated FP32 pair (>= 48 significant bits,
  *   advanced error-free), the step length is the FP32 number the stages use, and the norm
- *   accumulation and controller run in FP32: the attempt loop issues no FP64 instruction. */
-typedef enum { GS_FP64 = 0, GS_FP32_STAGES = 1, GS_FP32_DF = 2 } gs_precision;
+ *   accumulation and controller run in FP32: the attempt loop issues no FP64 instruction.
+ * GS_DF64: the state, the stages, the stage times, the error estimate and the dense outputs in
+ *   double-FP32 arithmetic (unevaluated pairs of FP32 numbers, ~48 significant bits, built from
+ *   error-free transformations), time and controller as GS_FP32_DF: tolerances near FP64's reach
+ *   without the FP64 pipe. Systems GS_SYS_ISOCHRONE, GS_SYS_PRECESSION and GS_SYS_LOGHALO (their
+ *   right-hand sides need only arithmetic and square roots); gs_solve and gs_vjp. */
+typedef enum { GS_FP64 = 0, GS_FP32_STAGES = 1, GS_FP32_DF = 2, GS_DF64 = 3 } gs_precision;
 
 /* GS_KERNEL_PLAIN: one thread per trajectory for its whole solve (a warp waits for its slowest
  *   member, Appendix A, Eq. cost). GS_KERNEL_PERSISTENT: persistent CTAs whose lanes take the next
@@ -144,7 +149,7 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
  *  trajectory with n accepted steps uses ceil(n / 32) chunks. slot = roundup16(state) + tail:
  *  GS_FP64 state 8 d bytes (FP64), tail 32 (t, tc, h, flag as FP64); GS_FP32_STAGES state 4 d (the
  *  FP32 high part, from which the stages are recomputed), tail 32; GS_FP32_DF state 4 d, tail 16
- *  (time pair, h, flag as FP32).
+ *  (time pair, h, flag as FP32); GS_DF64 state 8 d (df64 pairs), tail 16.
  */
 int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
            const double* t1, double rtol, double atol, int32_t K, const double* saveat,

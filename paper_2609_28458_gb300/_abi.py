@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(_PKG, "libgs.so")
 
 SYSTEMS = {"isochrone": 0, "mw": 1, "precession": 2, "quintessence": 3, "loghalo": 4}
 METHODS = {"tsit5": 0, "dopri5": 1, "vern7": 2}
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2, "df64": 3}
 KERNELS = {"auto": 0, "plain": 1, "persistent": 2}
 ORDER = {0: 5, 1: 5, 2: 7}
 

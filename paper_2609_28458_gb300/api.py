@@ -79,8 +79,8 @@ def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None, precision="f
     opt = opt or _abi.options(precision=precision)
     fixed = _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 0, 0.0)
     prec = opt.precision
-    state = (8 if prec == _abi.PRECISIONS["fp64"] else 4) * d
-    slot = (state + 15) // 16 * 16 + (16 if prec == _abi.PRECISIONS["fp32df"] else 32)
+    state = (8 if prec in (_abi.PRECISIONS["fp64"], _abi.PRECISIONS["df64"]) else 4) * d
+    slot = (state + 15) // 16 * 16 + (16 if prec in (_abi.PRECISIONS["fp32df"], _abi.PRECISIONS["df64"]) else 32)
     chunk = 16 + 32 * slot  # chunk header + 32 slots (gs.h)
     if n_accept is not None:
         chunks = int(((n_accept.to(torch.int64) + 31) // 32).sum().item()) + 1

@@ -28,7 +28,11 @@ def nvcc():
 
 
 def sources():
-    return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+    # heaviest translation units first (precession, then Verner 7), so that the parallel build's
+    # wall time is close to its longest unit
+    def cost(f):
+        return (0 if "precession" in f else 1 if "vern7" in f else 2, f)
+    return sorted((f for f in os.listdir(CSRC) if f.endswith(".cu")), key=cost)
 
 
 def _headers_mtime():

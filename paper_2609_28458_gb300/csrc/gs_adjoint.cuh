@@ -18,7 +18,7 @@ namespace gs {
 template <template <class> class SysT, class Tab, int PM>
 struct Adjoint {
   using T = Traj<SysT, Tab, PM>;
-  static constexpr bool F32 = T::F32, DF = T::DF;
+  static constexpr bool F32 = T::F32, DF = T::DF, DD = T::DD;
   using R = typename T::R;
   using Sys = typename T::Sys;
   static constexpr int D = T::D, NP = T::NP, S = Tab::S, NPA = T::NPA;
@@ -39,7 +39,7 @@ struct Adjoint {
         s[q] += v;
       }
     }
-    __device__ double get(int q) const { return double(s[q]) + double(c[q]); }
+    __device__ double get(int q) const { return to_f64(s[q]) + to_f64(c[q]); }
   };
 
   // Reverse through stages 0..jmax-1 of a step of length hh whose stage states are Y and whose
@@ -112,6 +112,19 @@ struct Adjoint {
 #pragma unroll
         for (int i = 0; i < D; i++) r.y[i] = f[i];
       }
+    } else if constexpr (DD) {
+      // (hi, lo) per component: two components per 16-byte load
+      const float4* f4 = reinterpret_cast<const float4*>(s);
+#pragma unroll
+      for (int q = 0; q < D / 2; q++) {
+        const float4 a = f4[q];
+        r.y[2 * q] = F2::pair(a.x, a.y);
+        r.y[2 * q + 1] = F2::pair(a.z, a.w);
+      }
+      if constexpr (D % 2 == 1) {
+        const float2 a = reinterpret_cast<const float2*>(s)[D - 1];
+        r.y[D - 1] = F2::pair(a.x, a.y);
+      }
     } else {
       const double2* f2 = reinterpret_cast<const double2*>(s);
 #pragma unroll
@@ -150,7 +163,14 @@ struct Adjoint {
     }
   }
   __device__ static R sigma(const SlotView& v, double sv) {
-    if constexpr (DF) {
+    if constexpr (DD) {  // as the forward: df64 fraction from the time pairs and the step's exact length
+      float svh, svl;
+      split_df(sv, svh, svl);
+      R sg = ((R(svh) + R(svl)) - (R(v.th) + R(v.tl))) / R(v.h);
+      if (val(sg) > 1.0f) sg = R(1.0f);
+      if (val(sg) < 0.0f) sg = R(0.0f);
+      return sg;
+    } else if constexpr (DF) {
       float svh, svl;
       split_df(sv, svh, svl);
       return fminf(fmaxf(__fdividef((svh - v.th) + (svl - v.tl), v.hf), 0.0f), 1.0f);
@@ -231,7 +251,10 @@ struct Adjoint {
     const long long n = tr.n;
     const double t0 = tr.t0, t1 = tr.t1;
     const int o = a % kChunk;
-    const SlotView cur = decode(nraw);
+    SlotView cur = decode(nraw);
+    // df64: the last step spanned the exact remainder t1 - t (exact in FP64 for the time pairs)
+    if constexpr (DD)
+      if (cur.last) cur.h = tr.t1 - cur.t;
 #pragma unroll
     for (int i = 0; i < D; i++) tr.y[i] = nraw.y[i];
     const int32_t pchunk = (o == 0 && a > 0) ? prev_chunk(pb, chunk) : chunk;
@@ -288,7 +311,7 @@ struct Adjoint {
           for (int i = 0; i < D; i++) ydir[i] += w[i];
         } else {
           // Verner 7: y(t_k) = shortened step of length sig*h from (t, y)
-          const double hs = double(sig) * cur.h;
+          const double hs = to_f64(sig) * cur.h;
           R ks[S][D], Ys[S][D], kbs[S][D];
           tr.stages(cur.t, hs, ks, Ys, Tab::NREV);
           const R hsr = R(hs);
@@ -329,7 +352,7 @@ struct Adjoint {
     }
     double* gy0 = pb.dLdy0 + n * D;
 #pragma unroll
-    for (int i = 0; i < D; i++) gy0[i] = double(ybar[i]);
+    for (int i = 0; i < D; i++) gy0[i] = to_f64(ybar[i]);
 #pragma unroll
     for (int q = 0; q < NP; q++) pb.dLdp[n * NP + q] = pacc.get(q);
     done = true;

@@ -47,12 +47,12 @@ int order_of(int32_t method) { return method == GS_VERN7 ? 7 : 5; }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// bytes of one tape slot: state (8 d bytes in every precision) padded to 16 bytes + a 32-byte tail
-// tape slot: the state at the step's start (FP64, or its FP32 high part), padded to 16 bytes,
-// then the times: t, tc, h, flag as FP64 (32 bytes), or th, tl, h, flag as FP32 (16 bytes, PM 2)
+// tape slot: the state at the step's start (FP64, df64 pairs, or its FP32 high part), padded to 16
+// bytes, then the times: t, tc, h, flag as FP64 (32 bytes), or th, tl, h, flag as FP32 (16 bytes,
+// PM 2 and 3)
 long long slot_bytes(int32_t d, int32_t prec) {
-  const long long state = (prec == GS_FP64 ? 8LL : 4LL) * d;
-  return (state + 15) / 16 * 16 + (prec == GS_FP32_DF ? 16 : 32);
+  const long long state = (prec == GS_FP64 || prec == GS_DF64 ? 8LL : 4LL) * d;
+  return (state + 15) / 16 * 16 + (prec == GS_FP32_DF || prec == GS_DF64 ? 16 : 32);
 }
 long long chunk_bytes(int32_t d, int32_t prec) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d, prec); }
 
@@ -114,7 +114,9 @@ int check_common(int32_t sys, int64_t N, const double* y0, const double* params,
   if (N > (int64_t(1) << 31) - 4096) return fail(GS_ERR_INVALID, "N too large (max 2^31 - 4096)");
   if (K < 0) return fail(GS_ERR_INVALID, "K < 0");
   if (opt->method < 0 || opt->method > 2) return fail(GS_ERR_INVALID, "unknown method %d", opt->method);
-  if (opt->precision < 0 || opt->precision > 2) return fail(GS_ERR_INVALID, "unknown precision %d", opt->precision);
+  if (opt->precision < 0 || opt->precision > 3) return fail(GS_ERR_INVALID, "unknown precision %d", opt->precision);
+  if (opt->precision == GS_DF64 && sys != GS_SYS_ISOCHRONE && sys != GS_SYS_PRECESSION && sys != GS_SYS_LOGHALO)
+    return fail(GS_ERR_INVALID, "GS_DF64 is available for the isochrone, precession and log-halo systems");
   if (opt->kernel < 0 || opt->kernel > 2) return fail(GS_ERR_INVALID, "unknown kernel %d", opt->kernel);
   if (opt->block_size < 0 || opt->block_size > 128 || (opt->block_size % 32) != 0)
     return fail(GS_ERR_INVALID, "block_size must be 0 or a multiple of 32 up to 128");
@@ -321,7 +323,7 @@ int jvp_on(int32_t system, int64_t N, const double* y0, const double* params, co
   int rc = check_common(system, N, y0, params, t0, t1, rtol, atol, K, saveat, opt, &d, &p);
   if (rc) return rc;
   if (m < 1) return fail(GS_ERR_INVALID, "m (number of sensitivity directions) must be >= 1");
-  if (opt->precision == GS_FP32_STAGES)
+  if (opt->precision == GS_FP32_STAGES || opt->precision == GS_DF64)
     return fail(GS_ERR_INVALID, "gs_jvp runs in GS_FP64 or GS_FP32_DF");
   if (N > 0 && ((K > 0 && (!y_out || !S_out)) || !status || !n_accept || !n_reject))
     return fail(GS_ERR_INVALID, "y_out, S_out, status and step counts must not be NULL");

@@ -1,8 +1,8 @@
-// Kernel instantiations for the precession system with the Dopri5 pair (forward plain and persistent,
-// reverse plain and persistent, all precision modes).
+// Kernel instantiations for the precession system with the Dopri5 pair: forward plain and persistent
+// and forward sensitivities, all precision modes (the reverse kernels are in the _rev unit).
 #include "gs_kernels.cuh"
 
 namespace gs {
-GS_DEFINE_METHOD(precession, Precession, Dopri5)
+GS_DEFINE_FORWARD_JVP(precession, Precession, Dopri5)
 
 }  // namespace gs

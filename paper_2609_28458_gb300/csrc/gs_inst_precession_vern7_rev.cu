@@ -1,0 +1,8 @@
+// Kernel instantiations for the precession system with the Vern7 pair: reverse (discrete adjoint)
+// plain and persistent, all precision modes.
+#include "gs_kernels.cuh"
+
+namespace gs {
+GS_DEFINE_REVERSE(precession, Precession, Vern7)
+
+}  // namespace gs

@@ -40,7 +40,7 @@ template <template <class> class SysT, class Tab, int PM, int MT = 0>
 struct Occupancy {
   static constexpr bool small = Tab::S <= 7 && SysT<float>::D <= 6 && MT == 0;
   static constexpr int fwd = (PM == 2 && small) ? GS_FWD_BLOCKS_FP32DF : (PM == 1 && small) ? 4 : 1;
-  static constexpr int rev = (PM != 0 && small) ? GS_REV_BLOCKS_FP32 : 1;
+  static constexpr int rev = ((PM == 1 || PM == 2) && small) ? GS_REV_BLOCKS_FP32 : 1;
 };
 
 template <template <class> class SysT, class Tab, int PM>
@@ -256,6 +256,9 @@ cudaError_t launch_forward_m(const Problem& pb, const LaunchCfg& c) {
   switch (c.precision) {
     case 0: return launch_forward_t<SysT, Tab, 0>(pb, c);
     case 1: return launch_forward_t<SysT, Tab, 1>(pb, c);
+    case 3:
+      if constexpr (HasDF64<SysT>::value) return launch_forward_t<SysT, Tab, 3>(pb, c);
+      else return cudaErrorInvalidValue;
     default: return launch_forward_t<SysT, Tab, 2>(pb, c);
   }
 }
@@ -264,6 +267,9 @@ cudaError_t launch_reverse_m(const Problem& pb, const LaunchCfg& c) {
   switch (c.precision) {
     case 0: return launch_reverse_t<SysT, Tab, 0>(pb, c);
     case 1: return launch_reverse_t<SysT, Tab, 1>(pb, c);
+    case 3:
+      if constexpr (HasDF64<SysT>::value) return launch_reverse_t<SysT, Tab, 3>(pb, c);
+      else return cudaErrorInvalidValue;
     default: return launch_reverse_t<SysT, Tab, 2>(pb, c);
   }
 }
@@ -292,16 +298,22 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
   cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p, \
                          const double* w, double* f, double* gy, double* gp, cudaStream_t s);
 
-#define GS_DEFINE_METHOD(name, SysT, Tab)                                                                 \
+// The heaviest instantiations (precession) put the reverse kernels in a translation unit of their own
+// (GS_DEFINE_FORWARD_JVP + GS_DEFINE_REVERSE) so that the two halves compile in parallel.
+#define GS_DEFINE_FORWARD_JVP(name, SysT, Tab)                                                            \
   cudaError_t forward_##name##_##Tab(const Problem& pb, const LaunchCfg& c) {                             \
     return launch_forward_m<SysT, Tab>(pb, c);                                                           \
-  }                                                                                                      \
-  cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c) {                             \
-    return launch_reverse_m<SysT, Tab>(pb, c);                                                           \
   }                                                                                                      \
   cudaError_t jvp_##name##_##Tab(const Problem& pb, const LaunchCfg& c, int mt) {                         \
     return launch_jvp_m<SysT, Tab>(pb, c, mt);                                                           \
   }
+#define GS_DEFINE_REVERSE(name, SysT, Tab)                                                                \
+  cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c) {                             \
+    return launch_reverse_m<SysT, Tab>(pb, c);                                                           \
+  }
+#define GS_DEFINE_METHOD(name, SysT, Tab) \
+  GS_DEFINE_FORWARD_JVP(name, SysT, Tab)  \
+  GS_DEFINE_REVERSE(name, SysT, Tab)
 #define GS_DEFINE_RHS(name, SysT)                                                                         \
   cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p,  \
                          const double* w, double* f, double* gy, double* gp, cudaStream_t s) {           \

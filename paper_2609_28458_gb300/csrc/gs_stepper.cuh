@@ -19,6 +19,9 @@
 //     itself (so state and time advance by the same number), and the norm accumulation and the
 //     controller are FP32. No FP64 instruction is left in the attempt loop; FP64 on GB300 issues
 //     at a small fraction of the FP32 rate.
+//  3  df64 stages: the state, the stages, the stage times, the error estimate and the dense outputs
+//     in double-FP32 arithmetic (gs_df64.cuh, ~48 bits), the time and the controller as in mode 2.
+//     For the tolerances FP32 cannot reach (rtol ~1e-10) without the FP64 pipe.
 //
 // Readings where the paper is silent (the same as the CPU oracle's): Hairer-Norsett-Wanner starting
 // step with exponent 1/(nu+1); the last step is clipped to land on t1 when h(1+4eps) >= t1 - t;
@@ -140,9 +143,10 @@ __device__ __forceinline__ void state_update(const Dual<float, M>& y, const Dual
 
 template <int PM>
 struct PrecTraits {
-  static constexpr bool F32 = PM != 0;
-  static constexpr bool DF = PM == 2;
-  using R = typename std::conditional<F32, float, double>::type;
+  static constexpr bool F32 = PM == 1 || PM == 2;  // FP32 stages with an FP32-pair state
+  static constexpr bool DF = PM == 2 || PM == 3;   // FP32-pair time, FP32 step size and controller
+  static constexpr bool DD = PM == 3;              // df64 stages and state
+  using R = typename std::conditional<F32, float, typename std::conditional<DD, F2, double>::type>::type;
 };
 
 // MT: number of forward-sensitivity directions carried with the state (0: none). With MT > 0 every
@@ -152,16 +156,17 @@ template <template <class> class SysT, class Tab, int PM, int MT = 0>
 struct Traj {
   static constexpr bool F32 = PrecTraits<PM>::F32;
   static constexpr bool DF = PrecTraits<PM>::DF;
+  static constexpr bool DD = PrecTraits<PM>::DD;
   using R = typename PrecTraits<PM>::R;
   using T = typename std::conditional<(MT > 0), Dual<R, (MT > 0 ? MT : 1)>, R>::type;
   using Sys = SysT<T>;
   static constexpr int D = Sys::D, NP = Sys::P, S = Tab::S;
   static constexpr int NPA = NP > 0 ? NP : 1;
   static constexpr int DL = F32 ? D : 1;
-  // slot layout: y[D] as FP64 (PM 0) or its FP32 high part (PM 1, 2; the reverse pass recomputes
-  // the stages from the high part alone, as the forward attempt does), padded to a multiple of 16
-  // bytes, then the tail: PM 0, 1: t, tc, h, flag (FP64, 32 bytes); PM 2: th, tl, h, flag (FP32,
-  // 16 bytes). Chunk headers and slots are multiples of 16 bytes, so every slot, state and tail is
+  // slot layout: y[D] as FP64 (PM 0), its FP32 high part (PM 1, 2; the reverse pass recomputes
+  // the stages from the high part alone, as the forward attempt does) or its df64 pairs (PM 3),
+  // padded to a multiple of 16 bytes, then the tail: PM 0, 1: t, tc, h, flag (FP64, 32 bytes);
+  // PM 2, 3: th, tl, h, flag (FP32, 16 bytes). Chunk headers and slots are multiples of 16 bytes, so every slot, state and tail is
   // 16-byte aligned for the vector loads and stores below.
   static constexpr int kStateBytes = (F32 ? 4 : 8) * D;
   static constexpr int kTailOff = (kStateBytes + 15) / 16 * 16;
@@ -175,8 +180,8 @@ struct Traj {
   T k1[D];    // f(t, y): the first stage of the next attempt
   T p[NPA];
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
-  float th, tl, hf, t1h, t1l, svh, svl;   // PM 2
-  float atolf, rtolf, lerr_prev;          // PM 1, 2
+  float th, tl, hf, t1h, t1l, svh, svl;   // PM 2, 3
+  float atolf, rtolf, lerr_prev;          // PM 1, 2, 3
   long long n;
   int32_t kk, nacc, nrej, status, chunk;
   bool done, failed, rec_ok, sv_ok;
@@ -185,6 +190,7 @@ struct Traj {
 
   __device__ __forceinline__ double yval(int i) const {
     if constexpr (F32) return double(val(y[i])) + double(ylo[i]);
+    else if constexpr (DD) return to_f64(y[i]);
     else return double(val(y[i]));
   }
 
@@ -195,6 +201,7 @@ struct Traj {
 #pragma unroll
     for (int i = 0; i < D; i++) {
       if constexpr (F32) o[i] = double(val(hi[i])) + double(val(lo[i]));
+      else if constexpr (DD) o[i] = to_f64(hi[i]);
       else o[i] = double(val(hi[i]));
     }
     if constexpr (MT > 0) {
@@ -307,8 +314,11 @@ struct Traj {
     h0 = fminf(h0, span);
     T y1[D], f1[D];
 #pragma unroll
-    for (int i = 0; i < D; i++) y1[i] = y[i] + (ylo[i] + h0 * k1[i]);
-    Sys::f((th + tl) + h0, y1, p, f1);
+    for (int i = 0; i < D; i++) {
+      if constexpr (DD) y1[i] = y[i] + R(h0) * k1[i];
+      else y1[i] = y[i] + (ylo[i] + h0 * k1[i]);
+    }
+    Sys::f((R(th) + R(tl)) + R(h0), y1, p, f1);
     float d2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; i++) {
@@ -416,7 +426,7 @@ struct Traj {
 #pragma unroll
           for (int l = 0; l < j; l++)
             if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
-          if constexpr (F32) Yj[i] = y[i] + hr * acc;
+          if constexpr (F32 || DD) Yj[i] = y[i] + hr * acc;
           else Yj[i] = y[i] + hh * acc;
           if (Y) Y[j][i] = Yj[i];
         }
@@ -439,11 +449,12 @@ struct Traj {
 #pragma unroll
         for (int j = 0; j < S; j++) acc = acc + w[j] * k[j][i];
         if constexpr (F32) { hi[i] = y[i]; lo[i] = ylo[i] + hr * acc; }
+        else if constexpr (DD) { hi[i] = y[i] + hr * acc; lo[i] = T(R(0)); }
         else { hi[i] = y[i] + hh * acc; lo[i] = T(R(0)); }
       }
     } else {
       T ks[S][D];
-      const double hs = double(sig) * hh;
+      const double hs = to_f64(sig) * hh;
       stages(tt, hs, ks, nullptr, Tab::NREV);
       const R hr = R(hs);
 #pragma unroll
@@ -453,6 +464,7 @@ struct Traj {
         for (int j = 0; j < Tab::NREV; j++)
           if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * ks[j][i];
         if constexpr (F32) { hi[i] = y[i]; lo[i] = ylo[i] + hr * acc; }
+        else if constexpr (DD) { hi[i] = y[i] + hr * acc; lo[i] = T(R(0)); }
         else { hi[i] = y[i] + hs * acc; lo[i] = T(R(0)); }
       }
     }
@@ -488,13 +500,17 @@ struct Traj {
 #pragma unroll
         for (int i = 0; i < D; i++) f[i] = y[i];
       }
+    } else if constexpr (DD) {
+      float2* f2 = reinterpret_cast<float2*>(slot);  // (hi, lo) per component, 8-byte aligned
+#pragma unroll
+      for (int i = 0; i < D; i++) f2[i] = make_float2(y[i].hi, y[i].lo);
     } else {
       double* f = reinterpret_cast<double*>(slot);
 #pragma unroll
       for (int i = 0; i < D; i++) f[i] = y[i];
     }
     if constexpr (DF) {
-      *reinterpret_cast<float4*>(slot + kTailOff) = make_float4(th, tl, hstep, last ? 1.0f : 0.0f);
+      *reinterpret_cast<float4*>(slot + kTailOff) = make_float4(th, tl, val(hstep), last ? 1.0f : 0.0f);
     } else {
       double* tail = reinterpret_cast<double*>(slot + kTailOff);
       tail[0] = t; tail[1] = tc; tail[2] = h; tail[3] = last ? 1.0 : 0.0;
@@ -549,6 +565,10 @@ struct Traj {
         if (!(hf >= 16.0f * kEps48 * tm)) { fail(isnan(hf) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW); return; }
       }
       hr = hf;
+      // df64: the last step spans the exact remainder t1 - t (an FP32 length would leave the final
+      // state one FP32 rounding of the step short of t1, far above df64's resolution)
+      if constexpr (DD)
+        if (last) hr = (R(t1h) + R(t1l)) - (R(th) + R(tl));
     } else {
       const double rem = (t1 - t) + tc;
       if (rem <= 0.0) { close_interval(pb); return; }
@@ -578,11 +598,11 @@ struct Traj {
           if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
         // FP32 modes: the stage state is y_hi + h sum a k; the low part of the state only enters the
         // update of the state itself (below), its effect on a stage is below the stage's FP32 rounding
-        if constexpr (F32) Yj[i] = y[i] + hr * acc;
+        if constexpr (F32 || DD) Yj[i] = y[i] + hr * acc;
         else Yj[i] = y[i] + h * acc;
         if (j == S - 1) Ylast[i] = Yj[i];
       }
-      if constexpr (DF) Sys::f((th + tl) + R(Tab::c(j)) * hr, Yj, p, k[j]);
+      if constexpr (DF) Sys::f((R(th) + R(tl)) + R(Tab::c(j)) * hr, Yj, p, k[j]);
       else Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
     }
     // ---- new state: y + h sum b_j k_j
@@ -599,6 +619,8 @@ struct Traj {
           if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * k[j][i];
         if constexpr (F32) {
           state_update(y[i], ylo[i] + hr * acc, ynew[i], ynlo[i]);
+        } else if constexpr (DD) {
+          ynew[i] = y[i] + hr * acc;
         } else {
           ynew[i] = y[i] + h * acc;
         }
@@ -626,6 +648,25 @@ struct Traj {
       err = sqrt(sq / D);
       accept = err <= 1.0;
       bad = isnan(err);
+    } else if constexpr (DD) {
+      // the weighted stage sum nearly cancels (it is the local error): it is formed in df64 and
+      // rounded to FP32 only afterwards; scale, ratio and sum of squares are FP32 as in mode 2
+      float sq = 0.0f;
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        R acc = R(0);
+#pragma unroll
+        for (int j = 0; j < S; j++)
+          if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * k[j][i];
+        const float e = val(hr * acc);
+        const float a = fabsf(val(y[i])), b = fabsf(val(ynew[i]));
+        const float sc = atolf + rtolf * (a > b ? a : b);
+        const float r = __fdividef(e, sc);
+        sq += r * r;
+      }
+      accept = sq <= float(D);
+      lerr = 0.5f * (__log2f(sq) - log2f(float(D)));
+      bad = isnan(sq);
     } else {
       // PM 1 accumulates the squares in FP64, PM 2 in FP32
       using Acc = typename std::conditional<PM == 1, double, float>::type;
@@ -658,7 +699,13 @@ struct Traj {
           at_end = last && svh == t1h && svl == t1l;
           const float dk = (svh - th) + (svl - tl);
           inside = last || dk <= hf;
-          sig = fminf(fmaxf(__fdividef(dk, hf), 0.0f), 1.0f);
+          if constexpr (DD) {  // the fraction of the step in df64, from the exact time pairs
+            sig = ((R(svh) + R(svl)) - (R(th) + R(tl))) / hr;
+            if (val(sig) > 1.0f) sig = R(1.0f);
+            if (val(sig) < 0.0f) sig = R(0.0f);
+          } else {
+            sig = fminf(fmaxf(__fdividef(dk, hf), 0.0f), 1.0f);
+          }
         } else {
           at_end = last && sv == t1;
           const double dk = (sv - t) + tc;
@@ -673,7 +720,8 @@ struct Traj {
           else write_out(pb, kk, ynew, ynew);
         } else if (inside) {
           T hi[D], lo[D];
-          if constexpr (DF) dense_point(double(th) + double(tl), double(hf), sig, k, hi, lo);
+          if constexpr (DD) dense_point(double(th) + double(tl), to_f64(hr), sig, k, hi, lo);
+          else if constexpr (DF) dense_point(double(th) + double(tl), double(hf), sig, k, hi, lo);
           else dense_point(t, h, sig, k, hi, lo);
           write_out(pb, kk, hi, lo);
         } else {
@@ -698,7 +746,7 @@ struct Traj {
         const float l = tl + e2;
         th = s + l;
         tl = l - (th - s);
-        if constexpr (!Tab::FSAL) Sys::f(th + tl, y, p, k1);
+        if constexpr (!Tab::FSAL) Sys::f(R(th) + R(tl), y, p, k1);
         hf = hf * factor_f(pb, lerr);
         lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;  // log2(1e-4)
       } else {

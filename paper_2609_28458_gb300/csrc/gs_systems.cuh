@@ -10,6 +10,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "gs_df64.cuh"
+
 namespace gs {
 
 // Gravitational constant in kpc^3 / (1e10 Msun Myr^2): IAU nominal GM_sun = 1.3271244e20 m^3/s^2,
@@ -479,5 +481,12 @@ struct Quintessence {
     gp[0] = a0_b; gp[1] = lam_b; gp[2] = om_b; gp[3] = or_b;
   }
 };
+
+// Systems whose right-hand sides use only what df64 provides (+, -, *, /, square roots): they are
+// instantiated in precision mode 3 as well.
+template <template <class> class SysT> struct HasDF64 { static constexpr bool value = false; };
+template <> struct HasDF64<Isochrone> { static constexpr bool value = true; };
+template <> struct HasDF64<LogHalo> { static constexpr bool value = true; };
+template <> struct HasDF64<Precession> { static constexpr bool value = true; };
 
 }  // namespace gs
