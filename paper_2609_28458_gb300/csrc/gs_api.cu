@@ -57,17 +57,60 @@ long long slot_bytes(int32_t d, int32_t prec) {
 long long chunk_bytes(int32_t d, int32_t prec) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d, prec); }
 
 // workspace: [0,256) header (queue counter at 0, pool counter at 8) | head[N] | n_rec[N] | pool
+// workspace: header (work counters), head[N], n_rec[N], the reverse pass's order[N] and its bucket
+// counters, then the tape pool
+constexpr int kOrderBuckets = 4096;
 struct Layout {
-  size_t header, head, nrec, pool, total_fixed;
+  size_t header, head, nrec, order, buckets, pool, total_fixed;
 };
 Layout layout(int64_t N) {
   Layout L;
   L.header = 0;
   L.head = 256;
   L.nrec = L.head + align256(size_t(N) * 4);
-  L.pool = L.nrec + align256(size_t(N) * 4);
+  L.order = L.nrec + align256(size_t(N) * 4);
+  L.buckets = L.order + align256(size_t(N) * 4);
+  L.pool = L.buckets + align256(size_t(kOrderBuckets) * 4);
   L.total_fixed = L.pool;
   return L;
+}
+
+// Longest-first order of the reverse pass: trajectories bucketed by recorded steps (8 per bucket,
+// the last bucket open-ended), buckets in descending length. A persistent lane then ends the sweep
+// on short trajectories (the pass ends when its slowest lane does), and the plain kernel's warps
+// hold trajectories of similar length. Equal-length trajectories keep no particular order: each
+// trajectory's arithmetic does not depend on it.
+__device__ __forceinline__ int order_bucket(int32_t nrec) {
+  int b = nrec > 0 ? (nrec >> 3) : 0;
+  if (b > kOrderBuckets - 1) b = kOrderBuckets - 1;
+  return kOrderBuckets - 1 - b;
+}
+__global__ void k_order_hist(long long N, const int32_t* nrec, unsigned int* cnt) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n < N) atomicAdd(&cnt[order_bucket(nrec[n])], 1u);
+}
+// exclusive scan of the kOrderBuckets counters in place (one block of 1024 threads, 4 each)
+__global__ void k_order_scan(unsigned int* cnt) {
+  __shared__ unsigned int part[1024];
+  const int t = threadIdx.x;
+  unsigned int v[4], sum = 0;
+#pragma unroll
+  for (int i = 0; i < 4; i++) { v[i] = cnt[4 * t + i]; sum += v[i]; }
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned int x = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  unsigned int run = part[t] - sum;  // exclusive prefix of this thread's four counters
+#pragma unroll
+  for (int i = 0; i < 4; i++) { cnt[4 * t + i] = run; run += v[i]; }
+}
+__global__ void k_order_scatter(long long N, const int32_t* nrec, unsigned int* pos, int32_t* order) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n < N) order[atomicAdd(&pos[order_bucket(nrec[n])], 1u)] = int32_t(n);
 }
 
 typedef cudaError_t (*launch_fn)(const gs::Problem&, const gs::LaunchCfg&);
@@ -296,6 +339,22 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   if (kernel == GS_KERNEL_PERSISTENT) {
     cudaError_t e0 = cudaMemsetAsync(pb.queue, 0, 4, s);
     if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
+  }
+  {  // longest-first order of the reverse pass
+    const Layout L = layout(N);
+    unsigned char* base = static_cast<unsigned char*>(workspace);
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(base + L.buckets);
+    int32_t* order = reinterpret_cast<int32_t*>(base + L.order);
+    cudaError_t e1 = cudaMemsetAsync(cnt, 0, size_t(kOrderBuckets) * 4, s);
+    if (e1 != cudaSuccess) return cuda_fail(e1, "cudaMemsetAsync");
+    const unsigned grid = unsigned((N + 255) / 256);
+    k_order_hist<<<grid, 256, 0, s>>>((long long)N, pb.tape.n_rec, cnt);
+    k_order_scan<<<1, 1024, 0, s>>>(cnt);
+    k_order_scatter<<<grid, 256, 0, s>>>((long long)N, pb.tape.n_rec, cnt, order);
+    e1 = cudaGetLastError();
+    if (e1 != cudaSuccess) return cuda_fail(e1, "order launch");
+    pb.work = order;
+    pb.n_work = N;
   }
   cudaError_t e = reverse_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "reverse launch");

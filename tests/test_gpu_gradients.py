@@ -149,7 +149,8 @@ def test_adjoint_status_conventions():
     g = gpu_vjp(e2, np.ones((4, 1, 6)), max_steps=100000)
     assert np.all(np.isnan(g["dLdy0"][1])) and np.all(np.isfinite(g["dLdy0"][[0, 2, 3]]))
     # a workspace too small for the tape: overflow flagged, gradients NaN, nothing else disturbed
-    g = gpu_vjp(e2, np.ones((4, 1, 6)), tape_nbytes=4096 + 4 * (16 + 32 * 80))
+    fixed = api.tape_bytes("mw", 4, n_accept=torch.zeros(4, dtype=torch.int32)) - (16 + 32 * 80)  # no chunk
+    g = gpu_vjp(e2, np.ones((4, 1, 6)), tape_nbytes=fixed + 4 * (16 + 32 * 80))
     over = (g["status"] & _abi.ST_TAPE_OVERFLOW) != 0
     assert over.any() and np.all(np.isnan(g["dLdy0"][over])) and np.all(np.isfinite(g["y"][~np.isnan(e2.y0).any(1)]))
 
