@@ -109,8 +109,24 @@ typedef struct {
                               every Newton iteration is launched (max_newton of them)
                               and work-list lengths stay on the device, so the calls
                               can be captured into a CUDA graph                        */
-  int32_t reserved;
+  int32_t order;           /* order in which the forward kernels take trajectories:
+                              GS_ORDER_AUTO (0): by cost_hint if given, else by the
+                              estimate for N >= 32768, else as stored; GS_ORDER_NATURAL
+                              (1): as stored, in gs_vjp's reverse pass too (otherwise
+                              ordered by the recorded step counts); GS_ORDER_ESTIMATE
+                              (2): longest first by the estimate
+                              (t1 - t0) ||f(t0, y0)/s|| / ||y0/s||, s = atol + rtol|y0|
+                              (one f evaluation per trajectory, the time-scale ratio of
+                              the starting-step heuristic); GS_ORDER_HINT (3): longest
+                              first by cost_hint. Results do not depend on the order  */
+  const int32_t* cost_hint;  /* [N] device array, e.g. the attempt counts of a previous
+                              solve of similar inputs (may be NULL)                    */
 } gs_options;
+
+#define GS_ORDER_AUTO 0
+#define GS_ORDER_NATURAL 1
+#define GS_ORDER_ESTIMATE 2
+#define GS_ORDER_HINT 3
 
 /* Fill *opt with the defaults above (Tsit5, FP64, auto kernel). */
 void gs_default_options(gs_options* opt);

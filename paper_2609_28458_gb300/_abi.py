@@ -13,6 +13,7 @@ SYSTEMS = {"isochrone": 0, "mw": 1, "precession": 2, "quintessence": 3, "loghalo
 METHODS = {"tsit5": 0, "dopri5": 1, "vern7": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp32df": 2, "df64": 3}
 KERNELS = {"auto": 0, "plain": 1, "persistent": 2}
+ORDERS = {"auto": 0, "natural": 1, "estimate": 2, "hint": 3}
 ORDER = {0: 5, 1: 5, 2: 7}
 
 ST_MAX_STEPS, ST_H_UNDERFLOW, ST_NONFINITE, ST_EMPTY_INTERVAL, ST_SAVEAT_OUTSIDE, ST_TAPE_OVERFLOW = 1, 2, 4, 8, 16, 32
@@ -33,7 +34,8 @@ class GsOptions(ctypes.Structure):
                 ("alpha_max", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("h0", ctypes.c_double), ("per_traj_saveat", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("record_tape", ctypes.c_int32), ("reuse_tape", ctypes.c_int32), ("tape_capacity", ctypes.c_int32),
-                ("sm_limit", ctypes.c_int32), ("graph_safe", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sm_limit", ctypes.c_int32), ("graph_safe", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("cost_hint", ctypes.c_void_p)]
 
 
 class GsProfileOptions(ctypes.Structure):
@@ -131,6 +133,10 @@ def options(method="tsit5", precision="fp64", kernel="auto", **kw):
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError("unknown option %s" % k)
+        if k == "order" and isinstance(v, str):
+            v = ORDERS[v]
+        if k == "cost_hint" and v is not None and not isinstance(v, (int, ctypes.c_void_p)):
+            v = v.data_ptr()  # a contiguous int32 device tensor kept alive by the caller
         setattr(o, k, v)
     return o
 

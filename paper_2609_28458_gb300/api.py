@@ -41,6 +41,19 @@ def _vec(x, n, dev, name):
     return _dev(x, dev, name).reshape(n)
 
 
+def _hint(kw, dev, N):
+    """cost_hint as a contiguous int32 device tensor of N entries (returned so the caller keeps it alive
+    for the call); the option passes its address."""
+    h = kw.get("cost_hint")
+    if h is None or isinstance(h, int):
+        return None
+    h = torch.as_tensor(h).to(device=dev, dtype=_i32).reshape(-1).contiguous()
+    if h.numel() != N:
+        raise ValueError("cost_hint must have one entry per trajectory")
+    kw["cost_hint"] = h
+    return h
+
+
 def _sysid(system):
     return _abi.SYSTEMS[system] if isinstance(system, str) else int(system)
 
@@ -103,6 +116,7 @@ def solve(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precis
     per_traj = saveat.dim() == 2
     K = saveat.shape[-1]
     steps_hint = kw.pop("steps_hint", 1024)
+    hint = _hint(kw, dev, N)  # noqa: F841 (kept alive through the call)
     opt = _abi.options(method, precision, kernel, per_traj_saveat=int(per_traj), record_tape=int(record_tape), **kw)
     if out is None:
         out = dict(y=torch.empty((N, K, d), dtype=torch.float64, device=dev),
@@ -139,6 +153,7 @@ def vjp(system, y0, params, t0, t1, saveat, rtol, atol, dLdy, method="tsit5", pr
     K = saveat.shape[-1]
     dLdy = _dev(dLdy, dev, "dLdy").reshape(N, K, d)
     steps_hint = kw.pop("steps_hint", 1024)
+    hint = _hint(kw, dev, N)  # noqa: F841 (kept alive through the call)
     opt = _abi.options(method, precision, kernel, per_traj_saveat=int(per_traj), reuse_tape=int(reuse_tape is not None),
                        **kw)
     if reuse_tape:
@@ -190,6 +205,7 @@ def jvp(system, y0, params, t0, t1, saveat, rtol, atol, dy0=None, dparams=None, 
         dy0 = dy0.reshape(N, d, m)
     if dparams is not None:
         dparams = dparams.reshape(N, p, m)
+    hint = _hint(kw, dev, N)  # noqa: F841 (kept alive through the call)
     opt = _abi.options(method, precision, "persistent", per_traj_saveat=int(per_traj), **kw)
     nbytes = _abi.lib().gs_workspace_bytes(_sysid(system), N, K, ctypes.byref(opt), 0, 0.0)
     wsb = _ws(dev, nbytes, workspace)

@@ -57,11 +57,11 @@ long long slot_bytes(int32_t d, int32_t prec) {
 long long chunk_bytes(int32_t d, int32_t prec) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d, prec); }
 
 // workspace: [0,256) header (queue counter at 0, pool counter at 8) | head[N] | n_rec[N] | pool
-// workspace: header (work counters), head[N], n_rec[N], the reverse pass's order[N] and its bucket
-// counters, then the tape pool
-constexpr int kOrderBuckets = 4096;
+// workspace: header (work counters), head[N], n_rec[N], a work list order[N] with its bucket
+// counters and the estimated costs cost[N] (longest-first ordering of the forward and reverse
+// launches), then the tape pool
 struct Layout {
-  size_t header, head, nrec, order, buckets, pool, total_fixed;
+  size_t header, head, nrec, order, buckets, cost, pool, total_fixed;
 };
 Layout layout(int64_t N) {
   Layout L;
@@ -70,48 +70,28 @@ Layout layout(int64_t N) {
   L.nrec = L.head + align256(size_t(N) * 4);
   L.order = L.nrec + align256(size_t(N) * 4);
   L.buckets = L.order + align256(size_t(N) * 4);
-  L.pool = L.buckets + align256(size_t(kOrderBuckets) * 4);
+  L.cost = L.buckets + align256(size_t(gs::kOrderBuckets) * 4);
+  L.pool = L.cost + align256(size_t(N) * 4);
   L.total_fixed = L.pool;
   return L;
 }
 
-// Longest-first order of the reverse pass: trajectories bucketed by recorded steps (8 per bucket,
-// the last bucket open-ended), buckets in descending length. A persistent lane then ends the sweep
-// on short trajectories (the pass ends when its slowest lane does), and the plain kernel's warps
-// hold trajectories of similar length. Equal-length trajectories keep no particular order: each
-// trajectory's arithmetic does not depend on it.
-__device__ __forceinline__ int order_bucket(int32_t nrec) {
-  int b = nrec > 0 ? (nrec >> 3) : 0;
-  if (b > kOrderBuckets - 1) b = kOrderBuckets - 1;
-  return kOrderBuckets - 1 - b;
+// Ordering of a forward launch (gs_options.order): the work list needs the workspace's fixed part.
+// (order and cost_hint are validated by check_common)
+int set_order(gs::Problem& pb, const gs_options* opt, int64_t N, void* ws, size_t ws_bytes) {
+  const Layout L = layout(N);
+  bool use = false;
+  if (opt->order == GS_ORDER_HINT || opt->order == GS_ORDER_ESTIMATE) use = true;
+  if (opt->order == GS_ORDER_AUTO) use = opt->cost_hint != nullptr || N >= 32768;
+  if (!use || !ws || ws_bytes < L.total_fixed) return GS_OK;  // as stored
+  unsigned char* base = static_cast<unsigned char*>(ws);
+  pb.cost_hint = (opt->order == GS_ORDER_ESTIMATE) ? nullptr : opt->cost_hint;
+  pb.ord_cost = reinterpret_cast<float*>(base + L.cost);
+  pb.ord_order = reinterpret_cast<int32_t*>(base + L.order);
+  pb.ord_cnt = reinterpret_cast<unsigned int*>(base + L.buckets);
+  return GS_OK;
 }
-__global__ void k_order_hist(long long N, const int32_t* nrec, unsigned int* cnt) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n < N) atomicAdd(&cnt[order_bucket(nrec[n])], 1u);
-}
-// exclusive scan of the kOrderBuckets counters in place (one block of 1024 threads, 4 each)
-__global__ void k_order_scan(unsigned int* cnt) {
-  __shared__ unsigned int part[1024];
-  const int t = threadIdx.x;
-  unsigned int v[4], sum = 0;
-#pragma unroll
-  for (int i = 0; i < 4; i++) { v[i] = cnt[4 * t + i]; sum += v[i]; }
-  part[t] = sum;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const unsigned int x = t >= off ? part[t - off] : 0u;
-    __syncthreads();
-    part[t] += x;
-    __syncthreads();
-  }
-  unsigned int run = part[t] - sum;  // exclusive prefix of this thread's four counters
-#pragma unroll
-  for (int i = 0; i < 4; i++) { cnt[4 * t + i] = run; run += v[i]; }
-}
-__global__ void k_order_scatter(long long N, const int32_t* nrec, unsigned int* pos, int32_t* order) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n < N) order[atomicAdd(&pos[order_bucket(nrec[n])], 1u)] = int32_t(n);
-}
+
 
 typedef cudaError_t (*launch_fn)(const gs::Problem&, const gs::LaunchCfg&);
 #define GS_PICK(kind, sysname)                                  \
@@ -161,6 +141,8 @@ int check_common(int32_t sys, int64_t N, const double* y0, const double* params,
   if (opt->precision == GS_DF64 && sys != GS_SYS_ISOCHRONE && sys != GS_SYS_PRECESSION && sys != GS_SYS_LOGHALO)
     return fail(GS_ERR_INVALID, "GS_DF64 is available for the isochrone, precession and log-halo systems");
   if (opt->kernel < 0 || opt->kernel > 2) return fail(GS_ERR_INVALID, "unknown kernel %d", opt->kernel);
+  if (opt->order < GS_ORDER_AUTO || opt->order > GS_ORDER_HINT) return fail(GS_ERR_INVALID, "unknown order %d", opt->order);
+  if (opt->order == GS_ORDER_HINT && !opt->cost_hint) return fail(GS_ERR_INVALID, "GS_ORDER_HINT needs cost_hint");
   if (opt->block_size < 0 || opt->block_size > 128 || (opt->block_size % 32) != 0)
     return fail(GS_ERR_INVALID, "block_size must be 0 or a multiple of 32 up to 128");
   if (!(rtol >= 0.0) || !(atol >= 0.0) || !(rtol + atol > 0.0) || !std::isfinite(rtol) || !std::isfinite(atol))
@@ -299,6 +281,8 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   }
+  rc = set_order(pb, opt, N, workspace, workspace_bytes);
+  if (rc) return rc;
   gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s, opt->sm_limit};
   cudaError_t e = forward_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");
@@ -322,6 +306,8 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
   rc = set_tape(pb, d, opt->precision, opt->tape_capacity, N, workspace, workspace_bytes);
   if (rc) return rc;
+  rc = set_order(pb, opt, N, workspace, workspace_bytes);  // of the forward re-solve
+  if (rc) return rc;
   pb.queue = static_cast<unsigned int*>(workspace);
   pb.dLdy = dLdy; pb.dLdy0 = dLdy0; pb.dLdp = dLdparams;
   const int kernel = opt->kernel == GS_KERNEL_AUTO ? GS_KERNEL_PERSISTENT : opt->kernel;
@@ -340,21 +326,16 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
     cudaError_t e0 = cudaMemsetAsync(pb.queue, 0, 4, s);
     if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
   }
-  {  // longest-first order of the reverse pass
+  if (opt->order != GS_ORDER_NATURAL) {  // longest-first order of the reverse pass, by the recorded step counts
     const Layout L = layout(N);
     unsigned char* base = static_cast<unsigned char*>(workspace);
-    unsigned int* cnt = reinterpret_cast<unsigned int*>(base + L.buckets);
     int32_t* order = reinterpret_cast<int32_t*>(base + L.order);
-    cudaError_t e1 = cudaMemsetAsync(cnt, 0, size_t(kOrderBuckets) * 4, s);
-    if (e1 != cudaSuccess) return cuda_fail(e1, "cudaMemsetAsync");
-    const unsigned grid = unsigned((N + 255) / 256);
-    k_order_hist<<<grid, 256, 0, s>>>((long long)N, pb.tape.n_rec, cnt);
-    k_order_scan<<<1, 1024, 0, s>>>(cnt);
-    k_order_scatter<<<grid, 256, 0, s>>>((long long)N, pb.tape.n_rec, cnt, order);
-    e1 = cudaGetLastError();
+    const cudaError_t e1 = gs::build_order((long long)N, nullptr, pb.tape.n_rec,
+                                           reinterpret_cast<unsigned int*>(base + L.buckets), order, s);
     if (e1 != cudaSuccess) return cuda_fail(e1, "order launch");
     pb.work = order;
     pb.n_work = N;
+    pb.ord_order = nullptr;
   }
   cudaError_t e = reverse_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "reverse launch");
@@ -399,6 +380,9 @@ int jvp_on(int32_t system, int64_t N, const double* y0, const double* params, co
     pb.work = work;
     pb.n_work = n_work;
     pb.n_work_dev = n_work_dev;  // at most n_work entries (checked by the writer of the list)
+  } else {
+    rc = set_order(pb, opt, N, workspace, workspace_bytes);
+    if (rc) return rc;
   }
   const int group = opt->method == GS_VERN7 ? 1 : 4;
   gs::LaunchCfg c{opt->method, opt->precision, GS_KERNEL_PERSISTENT, opt->block_size, s, opt->sm_limit};

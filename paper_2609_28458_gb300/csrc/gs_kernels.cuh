@@ -161,6 +161,112 @@ __global__ void k_rhs(long long M, const double* t, const double* y, const doubl
 }
 
 // ------------------------------------------------------------------------------------------------
+// Longest-first work lists. A persistent launch ends when its slowest lane does, so the trajectories
+// taken last should be the short ones; a plain launch's warps run as long as their longest member,
+// so members of similar length should share a warp. Costs are bucketed on a log scale (16 buckets per
+// octave, 4096 in all), buckets in descending cost; three small kernels and no host synchronisation.
+constexpr int kOrderBuckets = 4096;
+__device__ __forceinline__ int cost_bucket(float c) {
+  int b = 0;
+  if (c > 0.0f) {
+    b = int(floorf(log2f(c) * 16.0f)) + 2048;
+    b = b < 1 ? 1 : (b > kOrderBuckets - 1 ? kOrderBuckets - 1 : b);
+  }
+  return kOrderBuckets - 1 - b;  // zero or invalid cost: the last bucket
+}
+__device__ __forceinline__ float cost_of(const float* fc, const int32_t* ic, long long n) {
+  if (fc) return fc[n];
+  const int32_t v = ic[n];
+  return v > 0 ? float(v) : 0.0f;
+}
+static __global__ void k_order_hist(long long N, const float* fc, const int32_t* ic, unsigned int* cnt) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n < N) atomicAdd(&cnt[cost_bucket(cost_of(fc, ic, n))], 1u);
+}
+// exclusive scan of the kOrderBuckets counters in place (one block of 1024 threads, 4 each)
+static __global__ void k_order_scan(unsigned int* cnt) {
+  __shared__ unsigned int part[1024];
+  const int t = threadIdx.x;
+  unsigned int v[4], sum = 0;
+#pragma unroll
+  for (int i = 0; i < 4; i++) { v[i] = cnt[4 * t + i]; sum += v[i]; }
+  part[t] = sum;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned int x = t >= off ? part[t - off] : 0u;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  unsigned int run = part[t] - sum;
+#pragma unroll
+  for (int i = 0; i < 4; i++) { cnt[4 * t + i] = run; run += v[i]; }
+}
+static __global__ void k_order_scatter(long long N, const float* fc, const int32_t* ic, unsigned int* pos,
+                                       int32_t* order) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n < N) order[atomicAdd(&pos[cost_bucket(cost_of(fc, ic, n))], 1u)] = int32_t(n);
+}
+// order[0 .. N-1]: trajectory indices by descending cost (fc, or ic when fc is null)
+inline cudaError_t build_order(long long N, const float* fc, const int32_t* ic, unsigned int* cnt, int32_t* order,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cnt, 0, size_t(kOrderBuckets) * 4, s);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = unsigned((N + 255) / 256);
+  k_order_hist<<<grid, 256, 0, s>>>(N, fc, ic, cnt);
+  k_order_scan<<<1, 1024, 0, s>>>(cnt);
+  k_order_scatter<<<grid, 256, 0, s>>>(N, fc, ic, cnt, order);
+  return cudaGetLastError();
+}
+
+// Estimated cost of a trajectory: (t1 - t0) ||f(t0, y0)/s|| / ||y0/s||, s = atol + rtol |y0| (RMS
+// norms): the interval over the local time scale of the starting-step heuristic, from one FP32
+// evaluation of f. Empty or non-finite trajectories cost 0.
+template <template <class> class SysT>
+__global__ void k_cost_estimate(const Problem pb) {
+  using Sys = SysT<float>;
+  constexpr int D = Sys::D, NP = Sys::P, NPA = NP > 0 ? NP : 1;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= pb.N) return;
+  const double t0 = pb.t0[n], t1 = pb.t1[n];
+  float y[D], f[D], p[NPA];
+#pragma unroll
+  for (int i = 0; i < D; i++) y[i] = float(pb.y0[n * D + i]);
+#pragma unroll
+  for (int q = 0; q < NP; q++) p[q] = float(pb.params[n * NP + q]);
+  if (NP == 0) p[0] = 0.0f;
+  Sys::f(float(t0), y, p, f);
+  const float at = float(pb.atol), rt = float(pb.rtol);
+  float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; i++) {
+    const float sc = at + rt * fabsf(y[i]);
+    d0 += (y[i] / sc) * (y[i] / sc);
+    d1 += (f[i] / sc) * (f[i] / sc);
+  }
+  float c = float(t1 - t0) * sqrtf(d1 / fmaxf(d0, 1e-30f));
+  if (!(c > 0.0f) || !isfinite(c)) c = 0.0f;
+  pb.ord_cost[n] = c;
+}
+
+// The ordered copy of pb for a forward launch (pb itself when no ordering is asked for).
+template <template <class> class SysT>
+inline cudaError_t ordered(const Problem& pb, cudaStream_t s, Problem& q) {
+  q = pb;
+  if (!pb.ord_order || pb.work) return cudaSuccess;
+  const float* fc = nullptr;
+  if (!pb.cost_hint) {
+    k_cost_estimate<SysT><<<unsigned((pb.N + 255) / 256), 256, 0, s>>>(pb);
+    fc = pb.ord_cost;
+  }
+  const cudaError_t e = build_order(pb.N, fc, pb.cost_hint, pb.ord_cnt, pb.ord_order, s);
+  if (e != cudaSuccess) return e;
+  q.work = pb.ord_order;
+  q.n_work = pb.N;
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------------------
 inline int sm_count() {
   static int cached = 0;
   if (!cached) {
@@ -181,9 +287,12 @@ inline int persistent_grid(K kernel, int block, int sm_limit) {
 }
 
 template <template <class> class SysT, class Tab, int PM>
-cudaError_t launch_forward_t(const Problem& pb, const LaunchCfg& c) {
+cudaError_t launch_forward_t(const Problem& pb0, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
-  if (pb.n_work <= 0) return cudaSuccess;
+  if (pb0.n_work <= 0) return cudaSuccess;
+  Problem pb;
+  const cudaError_t eo = ordered<SysT>(pb0, c.stream, pb);
+  if (eo != cudaSuccess) return eo;
   if (c.kernel == 2) {
     auto kern = k_persist<SysT, Tab, PM>;
     long long grid = persistent_grid(kern, block, c.sm_limit);
@@ -218,9 +327,12 @@ cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
 
 // forward solve carrying MT sensitivity directions (persistent kernel)
 template <template <class> class SysT, class Tab, int PM, int MT>
-cudaError_t launch_jvp_t(const Problem& pb, const LaunchCfg& c) {
+cudaError_t launch_jvp_t(const Problem& pb0, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
-  if (pb.n_work <= 0) return cudaSuccess;
+  if (pb0.n_work <= 0) return cudaSuccess;
+  Problem pb;
+  const cudaError_t eo = ordered<SysT>(pb0, c.stream, pb);
+  if (eo != cudaSuccess) return eo;
   auto kern = k_persist<SysT, Tab, PM, MT>;
   long long grid = persistent_grid(kern, block, c.sm_limit);
   const long long need = (pb.n_work + block - 1) / block;

@@ -69,6 +69,12 @@ struct Problem {
   const int32_t* work;
   long long n_work;
   const unsigned int* n_work_dev;
+  // longest-first ordering of a forward launch (all null: as stored): either by cost_hint or by the
+  // estimate written to ord_cost; the order goes to ord_order, ord_cnt holds the bucket counters
+  const int32_t* cost_hint;
+  float* ord_cost;
+  int32_t* ord_order;
+  unsigned int* ord_cnt;
   int32_t K, per_traj;
   const double* y0;
   const double* params;

@@ -107,3 +107,16 @@ def test_solve_flat_argument_checks(lib):
     assert call(nbytes=1024) == _abi.GS_ERR_WORKSPACE
     assert call(ws=ctypes.c_void_p(8)) == _abi.GS_ERR_WORKSPACE
     assert call(N=0) == _abi.GS_OK
+
+
+def test_order_option_checks(lib):
+    """gs_options.order: unknown values and GS_ORDER_HINT without a hint are rejected on the host."""
+    fake = ctypes.c_void_p(256)
+    for order, hint in ((7, None), (-1, None), (_abi.ORDERS["hint"], None)):
+        o = _abi.options(kernel="plain", order=order)
+        if hint is not None:
+            o.cost_hint = hint
+        rc = lib.gs_solve(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
+                          None, 0, None)
+        assert rc == _abi.GS_ERR_INVALID, order
+    assert ctypes.sizeof(_abi.GsOptions) == 104
