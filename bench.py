@@ -116,24 +116,32 @@ def dist_env():
 
 
 # ------------------------------------------------------------------------------------------------
-def cpu_oracle_rate(e, rtol, target_s=12.0, nmax=200000):
+def cpu_oracle_rate(e, rtol, target_s=15.0, nmax=200000, n=None):
     """The CPU oracle (FP64 same-algorithm solve + forward-sensitivity gradient) on a bounded sample
-    of the workload, all host cores. Returns (solves/s, cores, sample description)."""
+    of the workload, all host cores: n orbits, or, when n is None, a 1024-orbit pilot sizes a sample
+    of about target_s seconds. Returns (solves/s, cores, sample description, n)."""
     import oracle as O
 
     cores = O.max_threads()
     rng = np.random.default_rng(7)
-    n = 256
-    while True:
+
+    def run(n):
         idx = np.sort(rng.choice(e.n, n, replace=False))
         s = e.subset(idx)
-        w = (rng.normal(size=(n, 1, 6)))
+        w = rng.normal(size=(n, 1, 6))
         t = time.perf_counter()
         O.grad("mw", s.y0, s.params, s.t0, s.t1, s.saveat, w, rtol=rtol, atol=rtol)
-        dt = time.perf_counter() - t
-        if dt * 4 > target_s or n * 4 > nmax:
-            return n / dt, cores, "%d of %d orbits (fwd + forward-sensitivity gradient), %.1f s" % (n, e.n, dt)
-        n *= 4
+        return time.perf_counter() - t
+
+    if n is None:
+        n = min(1024, nmax, e.n)
+        dt = run(n)
+        if dt < target_s / 4:
+            n = int(min(nmax, e.n, max(n, n * target_s / max(dt, 1e-9))))
+            dt = run(n)
+    else:
+        dt = run(n)
+    return n / dt, cores, "%d of %d orbits (fwd + forward-sensitivity gradient), %.1f s" % (n, e.n, dt), n
 
 
 def run_reference(args):
@@ -143,12 +151,14 @@ def run_reference(args):
     from paper_2609_28458_gb300 import workloads as W
 
     e = W.mw(n=N_ORBITS, seed=1000, t1=T1_MYR, rtol=RTOL_GRAD)
-    for _ in range(args.warmup):
-        cpu_oracle_rate(e, RTOL_GRAD, target_s=1.0, nmax=1024)
+    # one step: a sample of about 5 s of oracle work, sized once by the first warm-up step
+    n_step = None
+    for _ in range(max(args.warmup, 1)):
+        _, _, _, n_step = cpu_oracle_rate(e, RTOL_GRAD, target_s=5.0, n=n_step)
     t = time.perf_counter()
     rates = []
     for _ in range(args.steps):
-        r, cores, sample = cpu_oracle_rate(e, RTOL_GRAD, target_s=8.0)
+        r, cores, sample, _ = cpu_oracle_rate(e, RTOL_GRAD, n=n_step)
         rates.append(r)
     dt = time.perf_counter() - t
     value = float(np.median(rates))
@@ -378,7 +388,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
-        r, cores, sample = cpu_oracle_rate(e, RTOL_GRAD)
+        r, cores, sample, _ = cpu_oracle_rate(e, RTOL_GRAD)
         cpu = {"value": r, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -801,7 +811,8 @@ def run_mixed(args):
 def run_case(args):
     """Small profiling cases of the headline kernels (no JSON line): the seeded MW workload with
     --n orbits at --rtol, solved twice. 'fwd': persistent forward without a tape; 'fwdrev': forward
-    recording its tape, then the persistent reverse sweep."""
+    recording its tape, then the persistent reverse sweep. --t1-myr shortens the orbits so that a
+    case with several trajectories per lane keeps its tape to a few GB."""
     import torch
 
     from paper_2609_28458_gb300 import api
@@ -810,7 +821,7 @@ def run_case(args):
 
     gsbuild.build()
     dev = torch.device("cuda")
-    e = W.mw(n=args.n, seed=1000)
+    e = W.mw(n=args.n, seed=1000, t1=args.t1_myr)
     y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
     t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
     kw = dict(precision=args.precision, kernel="persistent")
@@ -841,6 +852,7 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--case", choices=["fwd", "fwdrev"], help="run a small profiling case instead")
+    ap.add_argument("--t1-myr", type=float, default=T1_MYR, help="orbit length of a --case run")
     ap.add_argument("--workload", default="mw",
                     choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "quintessence_flat",
                              "loghalo", "streams", "profile", "mixed"])

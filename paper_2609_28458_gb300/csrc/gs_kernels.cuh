@@ -179,9 +179,16 @@ __device__ __forceinline__ float cost_of(const float* fc, const int32_t* ic, lon
   const int32_t v = ic[n];
   return v > 0 ? float(v) : 0.0f;
 }
+// Both passes aggregate per warp: the lanes that share a bucket are counted (and placed) by one
+// atomic of their lowest lane. Ensembles of near-equal cost fall into a few buckets, where one atomic
+// per member would serialise on a single address. Blocks are whole warps (256 threads).
 static __global__ void k_order_hist(long long N, const float* fc, const int32_t* ic, unsigned int* cnt) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n < N) atomicAdd(&cnt[cost_bucket(cost_of(fc, ic, n))], 1u);
+  const bool ok = n < N;
+  const int b = ok ? cost_bucket(cost_of(fc, ic, n)) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  const int lane = threadIdx.x & 31;
+  if (ok && lane == __ffs(peers) - 1) atomicAdd(&cnt[b], unsigned(__popc(peers)));
 }
 // exclusive scan of the kOrderBuckets counters in place (one block of 1024 threads, 4 each)
 static __global__ void k_order_scan(unsigned int* cnt) {
@@ -205,7 +212,15 @@ static __global__ void k_order_scan(unsigned int* cnt) {
 static __global__ void k_order_scatter(long long N, const float* fc, const int32_t* ic, unsigned int* pos,
                                        int32_t* order) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n < N) order[atomicAdd(&pos[cost_bucket(cost_of(fc, ic, n))], 1u)] = int32_t(n);
+  const bool ok = n < N;
+  const int b = ok ? cost_bucket(cost_of(fc, ic, n)) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, b);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  unsigned base = 0;
+  if (ok && lane == leader) base = atomicAdd(&pos[b], unsigned(__popc(peers)));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  // lanes of one bucket keep their relative order, so runs of equal cost stay contiguous
+  if (ok) order[base + unsigned(__popc(peers & ((1u << lane) - 1u)))] = int32_t(n);
 }
 // order[0 .. N-1]: trajectory indices by descending cost (fc, or ic when fc is null)
 inline cudaError_t build_order(long long N, const float* fc, const int32_t* ic, unsigned int* cnt, int32_t* order,
