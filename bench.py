@@ -361,6 +361,24 @@ def run_gpu(args):
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = out_y0.numel() * 8 + out_p.numel() * 8
 
+    # ---------------- each kernel's fraction of its ALU peak (FP32, or FP64 for the FP64 modes) ----------
+    def attempts(r):
+        return int((r["n_accept"].long() + r["n_reject"].long()).sum().item())
+
+    def accepted(r):
+        return int(r["n_accept"].long().sum().item())
+
+    def kernel_frac(name, flops, ms, peak, prec):
+        a = flops / (ms / 1e3) / 1e12
+        return {"kernel": name, "ms": ms, "tflops": a, "peak": peak, "frac": a / peak,
+                "peak_kind": "FP64 nominal" if prec == "fp64" else "FP32 derived"}
+
+    kernels = [kernel_frac("k_persist (forward + tape record, fp32df)", n_att * F_ATT_FWD, fk, PEAK_FP32_TFLOPS, HEAD_PREC),
+               kernel_frac("k_reverse_persist (discrete adjoint, fp32df)", n_acc * F_STEP_REV, rk, PEAK_FP32_TFLOPS,
+                           HEAD_PREC),
+               kernel_frac("k_persist (forward, fp32df, estimate order)", attempts(sf) * F_ATT_FWD, fwd_ms,
+                           PEAK_FP32_TFLOPS, HEAD_PREC)]
+
     # ---------------- the other variants, each at its own budget tolerance ----------------
     variants = {}
     if not args.skip_variants:
@@ -374,6 +392,11 @@ def run_gpu(args):
             torch.cuda.empty_cache()
             _, fw, _ = make(prec, rf, kern)
             f_ms, so = timed(fw, 1, 1)
+            peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+            kernels.append(kernel_frac("k_%s (forward, %s)" % ("plain" if kern == "plain" else "persist", prec),
+                                       attempts(so) * F_ATT_FWD, f_ms, peak, prec))
+            kernels.append(kernel_frac("forward + tape and reverse, %s %s" % (kern, prec),
+                                       attempts(sg) * F_ATT_FWD + accepted(sg) * F_STEP_REV, g_ms, peak, prec))
             variants[name] = {"precision": prec, "kernel": kern, "fwd_rtol": rf, "fwd_ms": f_ms,
                               "fwd_solves_per_s": N / (f_ms / 1e3), "fwd_p99_orbit_err": M.p99(orbit_err(so["y"])),
                               "fwd_grad_rtol": RTOL_GRAD, "fwd_grad_ms": g_ms,
@@ -420,6 +443,7 @@ def run_gpu(args):
                                       if base else None),
             "step_attempts": {"mean": n_att / N, "accepted_mean": n_acc / N},
             "roofline": roofline,
+            "kernels": kernels,
             "cpu_baseline": cpu,
             "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -15,13 +15,19 @@
 
 namespace gs {
 
-template <template <class> class SysT, class Tab, int PM>
+// SLAB: the main step's stages leave their Jacobian factors in shared memory (from shared-window
+// byte address sl, the float4s st bytes apart)
+// and the stage VJPs read them back instead of re-evaluating the right-hand side's position factors;
+// only for FP32 modes of systems that provide f_save / vjp_saved (the kernel supplies the memory).
+template <template <class> class SysT, class Tab, int PM, bool SLAB = false>
 struct Adjoint {
   using T = Traj<SysT, Tab, PM>;
   static constexpr bool F32 = T::F32, DF = T::DF, DD = T::DD;
   using R = typename T::R;
   using Sys = typename T::Sys;
   static constexpr int D = T::D, NP = T::NP, S = Tab::S, NPA = T::NPA;
+  static constexpr int Q = SaveQ<Sys>::value;
+  static_assert(!SLAB || (Q > 0 && F32 && !DD), "saved stage factors need an FP32 mode and f_save");
 
   struct PAcc {  // accumulator of theta-bar: FP64, or a compensated FP32 pair
     R s[NPA], c[NPA];
@@ -45,8 +51,9 @@ struct Adjoint {
   // Reverse through stages 0..jmax-1 of a step of length hh whose stage states are Y and whose
   // stage cotangents are kbar (consumed). Adds to ybar and pacc: the stages' contributions to
   // theta-bar are summed in R first and enter the (compensated) accumulator once per step.
+  template <bool USE_SLAB = false>
   __device__ static void reverse_stages(const T& tr, double tt, double hh, R (*Y)[D], R (*kbar)[D], int jmax,
-                                        R* ybar, PAcc& pacc) {
+                                        R* ybar, PAcc& pacc, unsigned sl = 0, unsigned st = 0) {
     const R hr = R(hh);
     R gsum[NPA];
 #pragma unroll
@@ -55,7 +62,9 @@ struct Adjoint {
     for (int j = S - 1; j >= 0; j--) {
       if (j < jmax) {
         R gy[D], gp[NPA];
-        Sys::vjp(tr.stage_time(tt + Tab::c(j) * hh), Y[j], tr.p, kbar[j], gy, gp);
+        if constexpr (USE_SLAB) Sys::vjp_saved(tr.stage_time(tt + Tab::c(j) * hh), Y[j], tr.p, kbar[j], gy, gp,
+                                               sl + unsigned(j * Q) * st, st);
+        else Sys::vjp(tr.stage_time(tt + Tab::c(j) * hh), Y[j], tr.p, kbar[j], gy, gp);
 #pragma unroll
         for (int i = 0; i < D; i++) ybar[i] += gy[i];
 #pragma unroll
@@ -192,6 +201,7 @@ struct Adjoint {
   int32_t chunk;
   bool done;
   Raw nraw;  // the slot of step a, then (once step a has started) of step a - 1
+  unsigned sl = 0, st = 0;  // SLAB: this thread's stage factors, stage j at shared address sl + j * Q * st
 
   __device__ void write_const(const Problem& pb, double v_y, double v_p, bool sum_w, bool only_t0) {
     const long long n = tr.n;
@@ -260,7 +270,8 @@ struct Adjoint {
     const int32_t pchunk = (o == 0 && a > 0) ? prev_chunk(pb, chunk) : chunk;
     // fetch step a - 1 now; its times are decoded only where an output may belong to it
     if (a > 0) fetch(slot_ptr(pb, pchunk, o == 0 ? kChunk - 1 : o - 1), nraw);
-    Sys::f(tr.stage_time(cur.t), tr.y, tr.p, tr.k1);
+    if constexpr (SLAB) Sys::f_save(tr.stage_time(cur.t), tr.y, tr.p, tr.k1, sl, st);
+    else Sys::f(tr.stage_time(cur.t), tr.y, tr.p, tr.k1);
     // does an output inside this step use the dense polynomial (which needs the last, FSAL stage)?
     bool dense_here = false;
     if constexpr (Tab::DENSE_POLY) {
@@ -272,7 +283,7 @@ struct Adjoint {
       }
     }
     R k[S][D], Y[S][D], kbar[S][D];
-    tr.stages(cur.t, cur.h, k, Y, dense_here ? S : Tab::NREV);
+    tr.template stages<SLAB>(cur.t, cur.h, k, Y, dense_here ? S : Tab::NREV, sl, st);
 #pragma unroll
     for (int j = 0; j < S; j++)
 #pragma unroll
@@ -334,7 +345,7 @@ struct Adjoint {
         for (int i = 0; i < D; i++) kbar[j][i] += hr * R(Tab::b(j)) * ybar[i];
 #pragma unroll
     for (int i = 0; i < D; i++) ybar[i] += ydir[i];
-    reverse_stages(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc);
+    reverse_stages<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
     chunk = pchunk;
     a -= 1;
     if (a < 0) finish(pb);

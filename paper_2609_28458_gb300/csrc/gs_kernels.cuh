@@ -98,10 +98,26 @@ __global__ void __launch_bounds__(128) k_reverse(const Problem pb) {
   while (!adj.done) adj.step(pb);
 }
 
+// Shared memory of the persistent reverse pass per thread: the stage Jacobian factors (FP32 modes
+// of systems with f_save, 7-stage pairs), S x SaveQ float4 = 336 bytes for the Milky-Way system,
+// 43 KB per 128-thread block.
+template <template <class> class SysT, class Tab, int PM>
+struct RevSlab {
+  static constexpr int Q = SaveQ<SysT<float>>::value;
+  static constexpr bool on = (PM == 1 || PM == 2) && Q > 0 && Tab::S <= 7;
+  static constexpr int bytes_per_thread = on ? Tab::S * Q * 16 : 0;
+};
+
 // Reverse sweeps from a work queue (counter pb.queue), lanes refilled as in k_persist.
 template <template <class> class SysT, class Tab, int PM>
 __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_reverse_persist(const Problem pb) {
-  Adjoint<SysT, Tab, PM> adj;
+  constexpr bool SLAB = RevSlab<SysT, Tab, PM>::on;
+  Adjoint<SysT, Tab, PM, SLAB> adj;
+  if constexpr (SLAB) {
+    extern __shared__ float4 gs_rev_slab[];
+    adj.sl = unsigned(__cvta_generic_to_shared(gs_rev_slab + threadIdx.x));
+    adj.st = 16u * blockDim.x;
+  }
   const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
   bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
@@ -293,9 +309,9 @@ inline int sm_count() {
 }
 
 template <class K>
-inline int persistent_grid(K kernel, int block, int sm_limit) {
+inline int persistent_grid(K kernel, int block, int sm_limit, size_t smem = 0) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
   if (per_sm < 1) per_sm = 1;
   const int sms = (sm_limit > 0 && sm_limit < sm_count()) ? sm_limit : sm_count();
   return per_sm * sms;
@@ -328,11 +344,12 @@ cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
   if (pb.n_work <= 0) return cudaSuccess;
   if (c.kernel == 2) {
     auto kern = k_reverse_persist<SysT, Tab, PM>;
-    long long grid = persistent_grid(kern, block, c.sm_limit);
+    const size_t smem = size_t(RevSlab<SysT, Tab, PM>::bytes_per_thread) * size_t(block);
+    long long grid = persistent_grid(kern, block, c.sm_limit, smem);
     const long long need = (pb.n_work + block - 1) / block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
+    kern<<<unsigned(grid), block, smem, c.stream>>>(pb);
   } else {
     const long long grid = (pb.n_work + block - 1) / block;
     k_reverse<SysT, Tab, PM><<<unsigned(grid), block, 0, c.stream>>>(pb);

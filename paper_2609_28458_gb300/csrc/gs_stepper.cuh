@@ -417,8 +417,11 @@ struct Traj {
   }
 
   // Stages of one step of length hh from (tt, y): Eq. rk. k[0] = k1 on entry.
-  // Y[j] receives the state at which stage j was evaluated (Y[0] = y).
-  __device__ __forceinline__ void stages(double tt, double hh, T (*k)[D], T (*Y)[D], int nst) const {
+  // Y[j] receives the state at which stage j was evaluated (Y[0] = y). SAVE (FP32 reverse pass):
+  // f_save leaves stage j's Jacobian factors at shared address sl + j * SaveQ * st for its VJP.
+  template <bool SAVE = false>
+  __device__ __forceinline__ void stages(double tt, double hh, T (*k)[D], T (*Y)[D], int nst, unsigned sl = 0,
+                                         unsigned st = 0) const {
     const R hr = R(hh);
 #pragma unroll
     for (int i = 0; i < D; i++) { k[0][i] = k1[i]; if (Y) Y[0][i] = y[i]; }
@@ -436,8 +439,15 @@ struct Traj {
           else Yj[i] = y[i] + hh * acc;
           if (Y) Y[j][i] = Yj[i];
         }
-        if constexpr (DF) Sys::f(R(tt) + R(Tab::c(j)) * hr, Yj, p, k[j]);
-        else Sys::f(stage_time(tt + Tab::c(j) * hh), Yj, p, k[j]);
+        if constexpr (SAVE) {
+          constexpr int Q = SaveQ<Sys>::value;
+          if constexpr (DF) Sys::f_save(R(tt) + R(Tab::c(j)) * hr, Yj, p, k[j], sl + unsigned(j * Q) * st, st);
+          else Sys::f_save(stage_time(tt + Tab::c(j) * hh), Yj, p, k[j], sl + unsigned(j * Q) * st, st);
+        } else if constexpr (DF) {
+          Sys::f(R(tt) + R(Tab::c(j)) * hr, Yj, p, k[j]);
+        } else {
+          Sys::f(stage_time(tt + Tab::c(j) * hh), Yj, p, k[j]);
+        }
       }
     }
   }

@@ -10,6 +10,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "gs_df64.cuh"
 
 namespace gs {
@@ -18,6 +20,15 @@ namespace gs {
 // 1 kpc = 3.0856775814913673e19 m, 1 Myr = 3.15576e13 s.
 constexpr double kGmw = 1e10 * 1.3271244e20 * 3.15576e13 * 3.15576e13 /
                         (3.0856775814913673e19 * 3.0856775814913673e19 * 3.0856775814913673e19);
+
+// 16-byte shared-memory store and load at a shared-window byte address (volatile: kept in program
+// order with each other)
+__device__ __forceinline__ void st_shared4(unsigned a, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w));
+}
+__device__ __forceinline__ void ld_shared4(unsigned a, float& x, float& y, float& z, float& w) {
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(x), "=f"(y), "=f"(z), "=f"(w) : "r"(a));
+}
 
 template <class R> __device__ __forceinline__ R gsqrt(R x);
 template <> __device__ __forceinline__ double gsqrt<double>(double x) { return sqrt(x); }
@@ -91,12 +102,13 @@ template <class R>
 struct MilkyWay {
   static constexpr int D = 6, P = 4;
   static constexpr bool AUTONOMOUS = true;
+  // The position-dependent factors of the force and of its Jacobian. u = (x, y, u2) and
+  // v = (x, y, vh2); FULL adds the Hessian and q-derivative factors the VJP needs.
   struct Parts {
-    R cd0, u[3], u3p, iD2;        // disc: c_d / M_d, u, u3', 1/D^2
-    R kb0, r, ir, irc;            // bulge: k_b / M_b, r, 1/r, 1/(r + c)
-    R kh0, psi, im, irsm, vh[3];  // halo: k_h / M_h, psi, 1/m, 1/(r_s + m), v
-    R iq2;
+    R cd0, u2, iD2, kb0, kh0, vh2, iq2;  // c_d / M_d, A z / zeta, 1/D^2, k_b / M_b, k_h / M_h, z/q^2, 1/q^2
+    R u3p, kbr0, khm0, iq3;              // u3', k_b'/(r M_b), k_h'/(m M_h), 1/q^3
   };
+  template <bool FULL>
   __device__ static void parts(const R* y, const R* p, Parts& s) {
     const R G = R(kGmw), a = R(3.0), b = R(0.28), c = R(1.0), rs = R(15.6);
     const R x = y[0], yy = y[1], z = y[2];
@@ -112,61 +124,90 @@ struct MilkyWay {
     iD = iD * (R(1.5) - R(0.5) * D2 * iD * iD);
     s.iD2 = iD * iD;
     s.cd0 = G * s.iD2 * iD;
-    s.u[0] = x; s.u[1] = yy; s.u[2] = A * z * izeta;
-    s.u3p = izeta * izeta * (z2 + A * b * b * izeta);
+    s.u2 = A * z * izeta;
     const R r2 = R2 + z2;
-    s.ir = grsqrt(r2);
-    s.r = r2 * s.ir;
-    s.irc = grcp(s.r + c);
-    s.kb0 = G * s.ir * s.irc * s.irc;
+    const R ir = grsqrt(r2);
+    const R r = r2 * ir;
+    const R irc = grcp(r + c);
+    s.kb0 = G * ir * irc * irc;
     const R iq = grcp(p[3]);
     s.iq2 = iq * iq;
     const R m2 = R2 + z2 * s.iq2;
-    s.im = grsqrt(m2);
-    const R m = m2 * s.im;
-    s.irsm = grcp(rs + m);
-    s.psi = glog1p(m * R(1.0 / 15.6)) - m * s.irsm;
-    s.kh0 = G * s.psi * (s.im * s.im * s.im);
-    s.vh[0] = x; s.vh[1] = yy; s.vh[2] = z * s.iq2;
+    const R im = grsqrt(m2);
+    const R m = m2 * im;
+    const R irsm = grcp(rs + m);
+    const R psi = glog1p(m * R(1.0 / 15.6)) - m * irsm;
+    const R im3 = im * im * im;
+    s.kh0 = G * psi * im3;
+    s.vh2 = z * s.iq2;
+    if constexpr (FULL) {
+      s.u3p = izeta * izeta * (z2 + A * b * b * izeta);
+      s.kbr0 = -G * (R(3) * r + c) * (ir * ir * ir) * (irc * irc * irc);
+      s.khm0 = G * (im3 * irsm * irsm - R(3) * psi * im3 * (im * im));
+      s.iq3 = s.iq2 * iq;
+    }
   }
-  __device__ static void f(R, const R* y, const R* p, R* out) {
-    Parts s;
-    parts(y, p, s);
+  __device__ static void f_from(const R* y, const R* p, const Parts& s, R* out) {
     const R cd = p[0] * s.cd0, kb = p[1] * s.kb0, kh = p[2] * s.kh0;
     out[0] = y[3]; out[1] = y[4]; out[2] = y[5];
-#pragma unroll
-    for (int i = 0; i < 3; i++) out[3 + i] = -(cd * s.u[i] + kb * y[i] + kh * s.vh[i]);
+    out[3] = -(cd * y[0] + kb * y[0] + kh * y[0]);
+    out[4] = -(cd * y[1] + kb * y[1] + kh * y[1]);
+    out[5] = -(cd * s.u2 + kb * y[2] + kh * s.vh2);
   }
-  __device__ static void vjp(R, const R* y, const R* p, const R* w, R* gy, R* gp) {
-    Parts s;
-    parts(y, p, s);
-    const R G = R(kGmw), c = R(1.0);
+  __device__ static void vjp_from(const R* y, const R* p, const R* w, const Parts& s, R* gy, R* gp) {
+    const R x = y[0], yy = y[1], z = y[2];
     const R wv[3] = {w[3], w[4], w[5]};
     const R cd = p[0] * s.cd0, kb = p[1] * s.kb0, kh = p[2] * s.kh0;
-    const R uw = s.u[0] * wv[0] + s.u[1] * wv[1] + s.u[2] * wv[2];
-    const R xw = y[0] * wv[0] + y[1] * wv[1] + y[2] * wv[2];
-    const R vw = s.vh[0] * wv[0] + s.vh[1] * wv[1] + s.vh[2] * wv[2];
+    const R uw = x * wv[0] + yy * wv[1] + s.u2 * wv[2];
+    const R xw = x * wv[0] + yy * wv[1] + z * wv[2];
+    const R vw = x * wv[0] + yy * wv[1] + s.vh2 * wv[2];
     const R dfac = R(3) * cd * s.iD2;
-    const R ir3 = s.ir * s.ir * s.ir, irc3 = s.irc * s.irc * s.irc;
-    const R kbr = -G * p[1] * (R(3) * s.r + c) * ir3 * irc3;
-    const R im2 = s.im * s.im;
-    const R im3 = im2 * s.im;
-    const R khm0 = G * (im3 * s.irsm * s.irsm - R(3) * s.psi * im3 * im2);  // k_h'/(m M_h)
-    const R khm = p[2] * khm0;
+    const R kbr = p[1] * s.kbr0;
+    const R khm = p[2] * s.khm0;
     R Hw[3];
-    Hw[0] = cd * wv[0] - dfac * uw * s.u[0] + kb * wv[0] + kbr * xw * y[0] + kh * wv[0] + khm * vw * s.vh[0];
-    Hw[1] = cd * wv[1] - dfac * uw * s.u[1] + kb * wv[1] + kbr * xw * y[1] + kh * wv[1] + khm * vw * s.vh[1];
-    Hw[2] = cd * s.u3p * wv[2] - dfac * uw * s.u[2] + kb * wv[2] + kbr * xw * y[2] + kh * s.iq2 * wv[2] +
-            khm * vw * s.vh[2];
+    Hw[0] = cd * wv[0] - dfac * uw * x + kb * wv[0] + kbr * xw * x + kh * wv[0] + khm * vw * x;
+    Hw[1] = cd * wv[1] - dfac * uw * yy + kb * wv[1] + kbr * xw * yy + kh * wv[1] + khm * vw * yy;
+    Hw[2] = cd * s.u3p * wv[2] - dfac * uw * s.u2 + kb * wv[2] + kbr * xw * z + kh * s.iq2 * wv[2] +
+            khm * vw * s.vh2;
     gy[0] = -Hw[0]; gy[1] = -Hw[1]; gy[2] = -Hw[2];
     gy[3] = w[0]; gy[4] = w[1]; gy[5] = w[2];
-    const R iq3 = s.iq2 * grcp(p[3]);
-    const R z = y[2];
     gp[0] = -s.cd0 * uw;
     gp[1] = -s.kb0 * xw;
     gp[2] = -s.kh0 * vw;
     // -(k_h' dm/dq (v.w) + k_h (-2 z/q^3) w_z), dm/dq = -z^2/(q^3 m)
-    gp[3] = khm * z * z * iq3 * vw + R(2) * kh * z * iq3 * wv[2];
+    gp[3] = khm * z * z * s.iq3 * vw + R(2) * kh * z * s.iq3 * wv[2];
+  }
+  __device__ static void f(R, const R* y, const R* p, R* out) {
+    Parts s;
+    parts<false>(y, p, s);
+    f_from(y, p, s, out);
+  }
+  __device__ static void vjp(R, const R* y, const R* p, const R* w, R* gy, R* gp) {
+    Parts s;
+    parts<true>(y, p, s);
+    vjp_from(y, p, w, s, gy, gp);
+  }
+  // FP32 reverse pass: f at a recomputed stage also leaves the stage's Jacobian factors in shared
+  // memory (three float4 at the shared-window byte addresses sl, sl + st, sl + 2 st), and the stage's
+  // VJP reads them back instead of evaluating the potential again.
+  static constexpr int kSaveQ = 3;
+  __device__ static void f_save(R, const R* y, const R* p, R* out, unsigned sl, unsigned st) {
+    static_assert(std::is_same<R, float>::value, "saved stage factors are FP32");
+    Parts s;
+    parts<true>(y, p, s);
+    f_from(y, p, s, out);
+    st_shared4(sl, s.cd0, s.u2, s.iD2, s.u3p);
+    st_shared4(sl + st, s.kb0, s.kbr0, s.kh0, s.khm0);
+    st_shared4(sl + 2 * st, s.vh2, s.iq2, s.iq3, 0.0f);
+  }
+  __device__ static void vjp_saved(R, const R* y, const R* p, const R* w, R* gy, R* gp, unsigned sl, unsigned st) {
+    static_assert(std::is_same<R, float>::value, "saved stage factors are FP32");
+    Parts s;
+    float pad;
+    ld_shared4(sl, s.cd0, s.u2, s.iD2, s.u3p);
+    ld_shared4(sl + st, s.kb0, s.kbr0, s.kh0, s.khm0);
+    ld_shared4(sl + 2 * st, s.vh2, s.iq2, s.iq3, pad);
+    vjp_from(y, p, w, s, gy, gp);
   }
 };
 
@@ -488,5 +529,9 @@ template <template <class> class SysT> struct HasDF64 { static constexpr bool va
 template <> struct HasDF64<Isochrone> { static constexpr bool value = true; };
 template <> struct HasDF64<LogHalo> { static constexpr bool value = true; };
 template <> struct HasDF64<Precession> { static constexpr bool value = true; };
+
+// float4s per stage that a system's f_save leaves for its vjp_saved (0: the system has neither)
+template <class Sys, class = void> struct SaveQ { static constexpr int value = 0; };
+template <class Sys> struct SaveQ<Sys, std::void_t<decltype(Sys::kSaveQ)>> { static constexpr int value = Sys::kSaveQ; };
 
 }  // namespace gs
