@@ -17,7 +17,12 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# -ftz=true: FP32 denormals flush to zero. The FP32 paths never work near 1e-38 (states, stages,
+# error ratios and cotangents are all normal numbers), and without it every FP32 reciprocal,
+# reciprocal square root and logarithm carries a denormal-input fixup: measured on the 2^20-orbit
+# Milky-Way step, the flag takes the forward from 40.8 to 38.4 ms and the reverse from 41.8 to 39.6.
+# FP64 arithmetic is unaffected.
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
 
 def nvcc():
@@ -38,6 +43,7 @@ def sources():
 def _headers_mtime():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     hs.append(os.path.join(INCLUDE, "gs.h"))
+    hs.append(os.path.abspath(__file__))  # the compiler flags
     return max(os.path.getmtime(h) for h in hs)
 
 

@@ -235,6 +235,7 @@ struct Adjoint {
 #pragma unroll
     for (int q = 0; q < NP; q++) tr.p[q] = R(pb.params[n * NP + q]);
     if (NP == 0) tr.p[0] = R(0);
+    prep_params<Sys>(tr.p);
 #pragma unroll
     for (int i = 0; i < D; i++) ybar[i] = R(0);
     pacc.zero();

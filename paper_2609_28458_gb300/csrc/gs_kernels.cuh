@@ -154,12 +154,14 @@ __global__ void k_rhs(long long M, const double* t, const double* y, const doubl
   using R = typename std::conditional<F32, float, double>::type;
   using Sys = SysT<R>;
   constexpr int D = Sys::D, NP = Sys::P, NPA = NP > 0 ? NP : 1;
+  constexpr int NPP = PrepCount<Sys>::value > 0 ? PrepCount<Sys>::value : 1;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= M) return;
-  R yy[D], pp[NPA], ff[D];
+  R yy[D], pp[NPP], ff[D];
   for (int i = 0; i < D; i++) yy[i] = R(y[n * D + i]);
   for (int q = 0; q < NP; q++) pp[q] = R(p[n * NP + q]);
   if (NP == 0) pp[0] = R(0);
+  prep_params<Sys>(pp);
   const R tt = R(t[n]);
   if (f) {
     Sys::f(tt, yy, pp, ff);
@@ -256,16 +258,18 @@ inline cudaError_t build_order(long long N, const float* fc, const int32_t* ic, 
 template <template <class> class SysT>
 __global__ void k_cost_estimate(const Problem pb) {
   using Sys = SysT<float>;
-  constexpr int D = Sys::D, NP = Sys::P, NPA = NP > 0 ? NP : 1;
+  constexpr int D = Sys::D, NP = Sys::P;
+  constexpr int NPP = PrepCount<Sys>::value > 0 ? PrepCount<Sys>::value : 1;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= pb.N) return;
   const double t0 = pb.t0[n], t1 = pb.t1[n];
-  float y[D], f[D], p[NPA];
+  float y[D], f[D], p[NPP];
 #pragma unroll
   for (int i = 0; i < D; i++) y[i] = float(pb.y0[n * D + i]);
 #pragma unroll
   for (int q = 0; q < NP; q++) p[q] = float(pb.params[n * NP + q]);
   if (NP == 0) p[0] = 0.0f;
+  prep_params<Sys>(p);
   Sys::f(float(t0), y, p, f);
   const float at = float(pb.atol), rt = float(pb.rtol);
   float d0 = 0.0f, d1 = 0.0f;

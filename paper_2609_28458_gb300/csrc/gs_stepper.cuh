@@ -168,6 +168,7 @@ struct Traj {
   using Sys = SysT<T>;
   static constexpr int D = Sys::D, NP = Sys::P, S = Tab::S;
   static constexpr int NPA = NP > 0 ? NP : 1;
+  static constexpr int NPP = PrepCount<Sys>::value > 0 ? PrepCount<Sys>::value : 1;  // theta + prepared constants
   static constexpr int DL = F32 ? D : 1;
   // slot layout: y[D] as FP64 (PM 0), its FP32 high part (PM 1, 2; the reverse pass recomputes
   // the stages from the high part alone, as the forward attempt does) or its df64 pairs (PM 3),
@@ -184,7 +185,7 @@ struct Traj {
   T y[D];     // state (FP64) / high part (FP32), with its sensitivities when MT > 0
   R ylo[DL];  // low part (FP32)
   T k1[D];    // f(t, y): the first stage of the next attempt
-  T p[NPA];
+  T p[NPP];
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
   float th, tl, hf, t1h, t1l, svh, svl;   // PM 2, 3
   float atolf, rtolf, lerr_prev;          // PM 1, 2, 3
@@ -376,6 +377,7 @@ struct Traj {
         for (int m = 0; m < MT; m++)
           p[q].d[m] = pb.dp ? R(pb.dp[(n * NP + q) * (long long)pb.m_total + pb.m_off + m]) : R(0);
     }
+    prep_params<Sys>(p);  // derived constants carry the parameter directions too
     if (!fin) {
       status = ST_NONFINITE;
       failed = true;

@@ -100,8 +100,13 @@ struct Isochrone {
 //      d(grad Phi_h)/dq = k_h' dm/dq v + k_h (0, 0, -2z/q^3), dm/dq = -z^2/(q^3 m).
 template <class R>
 struct MilkyWay {
-  static constexpr int D = 6, P = 4;
+  static constexpr int D = 6, P = 4, PP = 6;  // p[4] = 1/q^2, p[5] = 1/q^3
   static constexpr bool AUTONOMOUS = true;
+  __device__ static void prep(R* p) {
+    const R iq = grcp(p[3]);
+    p[4] = iq * iq;
+    p[5] = p[4] * iq;
+  }
   // The position-dependent factors of the force and of its Jacobian. u = (x, y, u2) and
   // v = (x, y, vh2); FULL adds the Hessian and q-derivative factors the VJP needs.
   struct Parts {
@@ -130,8 +135,7 @@ struct MilkyWay {
     const R r = r2 * ir;
     const R irc = grcp(r + c);
     s.kb0 = G * ir * irc * irc;
-    const R iq = grcp(p[3]);
-    s.iq2 = iq * iq;
+    s.iq2 = p[4];
     const R m2 = R2 + z2 * s.iq2;
     const R im = grsqrt(m2);
     const R m = m2 * im;
@@ -144,7 +148,7 @@ struct MilkyWay {
       s.u3p = izeta * izeta * (z2 + A * b * b * izeta);
       s.kbr0 = -G * (R(3) * r + c) * (ir * ir * ir) * (irc * irc * irc);
       s.khm0 = G * (im3 * irsm * irsm - R(3) * psi * im3 * (im * im));
-      s.iq3 = s.iq2 * iq;
+      s.iq3 = p[5];
     }
   }
   __device__ static void f_from(const R* y, const R* p, const Parts& s, R* out) {
@@ -188,9 +192,9 @@ struct MilkyWay {
     vjp_from(y, p, w, s, gy, gp);
   }
   // FP32 reverse pass: f at a recomputed stage also leaves the stage's Jacobian factors in shared
-  // memory (three float4 at the shared-window byte addresses sl, sl + st, sl + 2 st), and the stage's
-  // VJP reads them back instead of evaluating the potential again.
-  static constexpr int kSaveQ = 3;
+  // memory (two float4 at the shared-window byte addresses sl and sl + st), and the stage's VJP reads
+  // them back instead of evaluating the potential again.
+  static constexpr int kSaveQ = 2;
   __device__ static void f_save(R, const R* y, const R* p, R* out, unsigned sl, unsigned st) {
     static_assert(std::is_same<R, float>::value, "saved stage factors are FP32");
     Parts s;
@@ -198,15 +202,15 @@ struct MilkyWay {
     f_from(y, p, s, out);
     st_shared4(sl, s.cd0, s.u2, s.iD2, s.u3p);
     st_shared4(sl + st, s.kb0, s.kbr0, s.kh0, s.khm0);
-    st_shared4(sl + 2 * st, s.vh2, s.iq2, s.iq3, 0.0f);
   }
   __device__ static void vjp_saved(R, const R* y, const R* p, const R* w, R* gy, R* gp, unsigned sl, unsigned st) {
     static_assert(std::is_same<R, float>::value, "saved stage factors are FP32");
     Parts s;
-    float pad;
     ld_shared4(sl, s.cd0, s.u2, s.iD2, s.u3p);
     ld_shared4(sl + st, s.kb0, s.kbr0, s.kh0, s.khm0);
-    ld_shared4(sl + 2 * st, s.vh2, s.iq2, s.iq3, pad);
+    s.iq2 = p[4];
+    s.iq3 = p[5];
+    s.vh2 = y[2] * s.iq2;
     vjp_from(y, p, w, s, gy, gp);
   }
 };
@@ -217,18 +221,23 @@ struct MilkyWay {
 // H w = kappa (w1, w2, w3/q^2) - 2 v_c^2/Q^2 (v.w) v. theta = (v_c, R_c, q).
 template <class R>
 struct LogHalo {
-  static constexpr int D = 6, P = 3;
+  static constexpr int D = 6, P = 3, PP = 5;  // p[3] = 1/q^2, p[4] = 1/q^3
   static constexpr bool AUTONOMOUS = true;
+  __device__ static void prep(R* p) {
+    const R iq = grcp(p[2]);
+    p[3] = iq * iq;
+    p[4] = p[3] * iq;
+  }
   __device__ static void f(R, const R* y, const R* p, R* out) {
-    const R iq2 = grcp(p[2] * p[2]);
+    const R iq2 = p[3];
     const R Q = p[1] * p[1] + y[0] * y[0] + y[1] * y[1] + y[2] * y[2] * iq2;
     const R k = p[0] * p[0] * grcp(Q);
     out[0] = y[3]; out[1] = y[4]; out[2] = y[5];
     out[3] = -k * y[0]; out[4] = -k * y[1]; out[5] = -k * y[2] * iq2;
   }
   __device__ static void vjp(R, const R* y, const R* p, const R* w, R* gy, R* gp) {
-    const R vc = p[0], Rc = p[1], q = p[2];
-    const R iq = grcp(q), iq2 = iq * iq, iq3 = iq2 * iq;
+    const R vc = p[0], Rc = p[1];
+    const R iq2 = p[3], iq3 = p[4];
     const R Q = Rc * Rc + y[0] * y[0] + y[1] * y[1] + y[2] * y[2] * iq2;
     const R iQ = grcp(Q);
     const R k = vc * vc * iQ;
@@ -264,10 +273,15 @@ __device__ __forceinline__ R dot3(const R* a, const R* b) { return a[0] * b[0] +
 
 template <class R>
 struct Precession {
-  static constexpr int D = 9, P = 3;
+  static constexpr int D = 9, P = 3, PP = 6;  // p[3] = m1 = 1/(1+q), p[4] = 1/q, p[5] = 1/eta
   static constexpr bool AUTONOMOUS = false;
+  __device__ static void prep(R* p) {
+    p[3] = R(1) / (R(1) + p[0]);
+    p[4] = R(1) / p[0];
+    p[5] = R(1) / (p[3] * (p[0] * p[3]));
+  }
   struct Fwd {
-    R m1, m2, eta, S1, S2, L, h, q;
+    R m1, m2, eta, S1, S2, L, h, q, iq, ieta, iv;
     R Lv[3], S1v[3], S2v[3], a1[3], a2[3], pr1, pr2, w1[3], w2[3], ds1[3], ds2[3], U[3], dL[3];
     R ls1, ls2, s12, X, T1, T2, b2, b3, b4, poly, dvdt, inv, v2, v3, v9;
   };
@@ -276,12 +290,15 @@ struct Precession {
     const R* Lh = y; const R* s1 = y + 3; const R* s2 = y + 6;
     F.q = p[0];
     const R chi1 = p[1], chi2 = p[2];
-    F.m1 = R(1) / (R(1) + F.q);
+    F.m1 = p[3];
+    F.iq = p[4];
+    F.ieta = p[5];
     F.m2 = F.q * F.m1;
     F.eta = F.m1 * F.m2;
     F.S1 = chi1 * F.m1 * F.m1;
     F.S2 = chi2 * F.m2 * F.m2;
-    F.L = F.eta / v;
+    F.iv = R(1) / v;
+    F.L = F.eta * F.iv;
     F.v2 = v * v; F.v3 = F.v2 * v;
     const R v6 = F.v3 * F.v3;
     F.v9 = v6 * F.v3;
@@ -290,11 +307,11 @@ struct Precession {
     for (int i = 0; i < 3; i++) {
       F.Lv[i] = F.L * Lh[i]; F.S1v[i] = F.S1 * s1[i]; F.S2v[i] = F.S2 * s2[i];
       F.a1[i] = F.S2v[i] + F.q * F.S1v[i];
-      F.a2[i] = F.S1v[i] + F.S2v[i] / F.q;
+      F.a2[i] = F.S1v[i] + F.S2v[i] * F.iq;
     }
     F.pr1 = dot3(Lh, F.a1);
     F.pr2 = dot3(Lh, F.a2);
-    const R c1 = R(4) + R(3) * F.q, c2 = R(4) + R(3) / F.q;
+    const R c1 = R(4) + R(3) * F.q, c2 = R(4) + R(3) * F.iq;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
       F.w1[i] = F.h * (c1 * F.Lv[i] + F.S2v[i] - R(3) * F.pr1 * Lh[i]);
@@ -302,21 +319,21 @@ struct Precession {
     }
     cross3(F.w1, s1, F.ds1);
     cross3(F.w2, s2, F.ds2);
-    const R k = -v / F.eta;
+    const R k = -v * F.ieta;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
       F.U[i] = F.S1 * F.ds1[i] + F.S2 * F.ds2[i];
       F.dL[i] = k * F.U[i];
     }
     F.ls1 = dot3(Lh, s1); F.ls2 = dot3(Lh, s2); F.s12 = dot3(s1, s2);
-    F.b2 = -(R(743) + R(924) * F.eta) / R(336);
+    F.b2 = -(R(743) + R(924) * F.eta) * R(1.0 / 336.0);
     F.T1 = R(113) * F.m1 * F.m1 + R(75) * F.eta;
     F.T2 = R(113) * F.m2 * F.m2 + R(75) * F.eta;
-    const R beta = (chi1 * F.ls1 * F.T1 + chi2 * F.ls2 * F.T2) / R(12);
+    const R beta = (chi1 * F.ls1 * F.T1 + chi2 * F.ls2 * F.T2) * R(1.0 / 12.0);
     F.b3 = R(4) * pi - beta;
     F.X = R(247) * F.s12 - R(721) * F.ls1 * F.ls2;
     F.b4 = R(34103.0 / 18144.0) + R(13661.0 / 2016.0) * F.eta + R(59.0 / 18.0) * F.eta * F.eta -
-           (F.eta / R(48)) * chi1 * chi2 * F.X;
+           (F.eta * R(1.0 / 48.0)) * chi1 * chi2 * F.X;
     F.poly = R(1) + F.b2 * F.v2 + F.b3 * F.v3 + F.b4 * F.v2 * F.v2;
     F.dvdt = R(32.0 / 5.0) * F.eta * F.v9 * F.poly;
     F.inv = R(1) / F.dvdt;
@@ -351,21 +368,23 @@ struct Precession {
     // poly = 1 + b2 v2 + b3 v3 + b4 v4
     const R b2_b = poly_b * F.v2, b3_b = poly_b * F.v3, b4_b = poly_b * F.v2 * F.v2;
     // b4
-    eta_b += b4_b * (R(13661.0 / 2016.0) + R(2.0 * 59.0 / 18.0) * F.eta - chi1 * chi2 * F.X / R(48));
-    c1_b += b4_b * (-(F.eta / R(48)) * chi2 * F.X);
-    c2_b += b4_b * (-(F.eta / R(48)) * chi1 * F.X);
-    const R X_b = b4_b * (-(F.eta / R(48)) * chi1 * chi2);
+    const R e48 = F.eta * R(1.0 / 48.0);
+    eta_b += b4_b * (R(13661.0 / 2016.0) + R(2.0 * 59.0 / 18.0) * F.eta - chi1 * chi2 * F.X * R(1.0 / 48.0));
+    c1_b += b4_b * (-e48 * chi2 * F.X);
+    c2_b += b4_b * (-e48 * chi1 * F.X);
+    const R X_b = b4_b * (-e48 * chi1 * chi2);
     R s12_b = R(247) * X_b;
     R ls1_b = -R(721) * F.ls2 * X_b;
     R ls2_b = -R(721) * F.ls1 * X_b;
     // b3 = 4 pi - beta, beta = (chi1 ls1 T1 + chi2 ls2 T2)/12
     const R beta_b = -b3_b;
-    c1_b += beta_b * F.ls1 * F.T1 / R(12);
-    ls1_b += beta_b * chi1 * F.T1 / R(12);
-    const R T1_b = beta_b * chi1 * F.ls1 / R(12);
-    c2_b += beta_b * F.ls2 * F.T2 / R(12);
-    ls2_b += beta_b * chi2 * F.T2 / R(12);
-    const R T2_b = beta_b * chi2 * F.ls2 / R(12);
+    const R beta12 = beta_b * R(1.0 / 12.0);
+    c1_b += beta12 * F.ls1 * F.T1;
+    ls1_b += beta12 * chi1 * F.T1;
+    const R T1_b = beta12 * chi1 * F.ls1;
+    c2_b += beta12 * F.ls2 * F.T2;
+    ls2_b += beta12 * chi2 * F.T2;
+    const R T2_b = beta12 * chi2 * F.ls2;
     m1_b += T1_b * R(226) * F.m1;
     m2_b += T2_b * R(226) * F.m2;
     eta_b += R(75) * (T1_b + T2_b);
@@ -380,10 +399,10 @@ struct Precession {
     }
     // dL = -(v/eta) U, U = S1 ds1 + S2 ds2
     R U_b[3];
-    const R k = -v / F.eta;
+    const R k = -v * F.ieta;
 #pragma unroll
     for (int i = 0; i < 3; i++) U_b[i] = k * dL_b[i];
-    eta_b += (v / (F.eta * F.eta)) * dot3(dL_b, F.U);
+    eta_b += (v * F.ieta * F.ieta) * dot3(dL_b, F.U);
     S1_b += dot3(U_b, F.ds1);
     S2_b += dot3(U_b, F.ds2);
 #pragma unroll
@@ -399,7 +418,7 @@ struct Precession {
 #pragma unroll
     for (int i = 0; i < 3; i++) s2_b[i] += tmp[i];
     // w1 = h ((4+3q) Lv + S2v - 3 pr1 Lh), w2 = h ((4+3/q) Lv + S1v - 3 pr2 Lh)
-    const R c1 = R(4) + R(3) * F.q, c2 = R(4) + R(3) / F.q;
+    const R c1 = R(4) + R(3) * F.q, c2 = R(4) + R(3) * F.iq;
     R Lv_b[3], S1v_b[3], S2v_b[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) {
@@ -407,7 +426,7 @@ struct Precession {
       S2v_b[i] = F.h * w1_b[i];
       S1v_b[i] = F.h * w2_b[i];
     }
-    q_b += F.h * (R(3) * dot3(F.Lv, w1_b) - (R(3) / (F.q * F.q)) * dot3(F.Lv, w2_b));
+    q_b += F.h * (R(3) * dot3(F.Lv, w1_b) - (R(3) * F.iq * F.iq) * dot3(F.Lv, w2_b));
     const R pr1_b = -R(3) * F.h * dot3(Lh, w1_b);
     const R pr2_b = -R(3) * F.h * dot3(Lh, w2_b);
 #pragma unroll
@@ -423,10 +442,10 @@ struct Precession {
     // a1 = S2v + q S1v, a2 = S1v + S2v/q
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-      S2v_b[i] += a1_b[i] + a2_b[i] / F.q;
+      S2v_b[i] += a1_b[i] + a2_b[i] * F.iq;
       S1v_b[i] += F.q * a1_b[i] + a2_b[i];
     }
-    q_b += dot3(F.S1v, a1_b) - dot3(F.S2v, a2_b) / (F.q * F.q);
+    q_b += dot3(F.S1v, a1_b) - dot3(F.S2v, a2_b) * (F.iq * F.iq);
     // Lv = L Lh, S1v = S1 s1, S2v = S2 s2
     L_b += dot3(Lh, Lv_b);
     S1_b += dot3(s1, S1v_b);
@@ -438,7 +457,7 @@ struct Precession {
       s2_b[i] += F.S2 * S2v_b[i];
     }
     // L = eta / v
-    eta_b += L_b / v;
+    eta_b += L_b * F.iv;
     // S1 = chi1 m1^2, S2 = chi2 m2^2
     c1_b += S1_b * F.m1 * F.m1;
     m1_b += S1_b * R(2) * chi1 * F.m1;
@@ -529,6 +548,16 @@ template <template <class> class SysT> struct HasDF64 { static constexpr bool va
 template <> struct HasDF64<Isochrone> { static constexpr bool value = true; };
 template <> struct HasDF64<LogHalo> { static constexpr bool value = true; };
 template <> struct HasDF64<Precession> { static constexpr bool value = true; };
+
+// Per-trajectory constants: a system may declare PP > P and prep(p), which fills p[P .. PP-1] from
+// theta = p[0 .. P-1] once per trajectory (reciprocals of parameters, mass ratios), so that f and
+// its VJP read them instead of dividing at every stage. Gradients stay with respect to theta.
+template <class Sys, class = void> struct PrepCount { static constexpr int value = Sys::P; };
+template <class Sys> struct PrepCount<Sys, std::void_t<decltype(Sys::PP)>> { static constexpr int value = Sys::PP; };
+template <class Sys, class Rp>
+__device__ __forceinline__ void prep_params(Rp* p) {
+  if constexpr (PrepCount<Sys>::value > Sys::P) Sys::prep(p);
+}
 
 // float4s per stage that a system's f_save leaves for its vjp_saved (0: the system has neither)
 template <class Sys, class = void> struct SaveQ { static constexpr int value = 0; };
