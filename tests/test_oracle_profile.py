@@ -1,7 +1,7 @@
 """Pins of the oracle's profile-likelihood Gauss-Newton fit (Sec. 4.3, Appendix C, Eq. de-gn):
 
-* r_d from the Aubourg et al. (2015) fitting formula reproduces the Planck 2018 sound horizon
-  (147.09 Mpc) at Planck's densities;
+* r_d from the Aubourg et al. (2015) fitting formula reproduces the Planck 2018 sound horizon at
+  Planck's densities (tests/golden/planck2018_sound_horizon.txt, two parameter sets);
 * the projection of the whitened supernova residuals equals the analytic minimum over the absolute
   magnitude M of (v - M 1)^T C^{-1} (v - M 1);
 * the spline through the 64 nodes gives the BAO distances and supernova magnitudes of a direct
@@ -10,6 +10,8 @@
 * on noiseless data the fit returns the generating (Om, H0) with chi^2 ~ 0, and on a noisy mock it
   ends at a stationary point (decrement < 1e-6) that passes the paper's convergence test.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -28,9 +30,14 @@ def setup():
 
 
 def test_sound_horizon_matches_planck():
-    h = 0.6766
-    om = (0.14175 + P.OMEGA_NU) / h ** 2     # omega_c + omega_b = 0.14175 (Planck 2018)
-    assert abs(P.rd_aubourg(om, 100 * h, 0.02242) - 147.09) < 0.2
+    # tests/golden/planck2018_sound_horizon.txt: Planck 2018 VI, Table 2 (densities and r_drag);
+    # 0.1 Mpc is three times the formula's stated 0.02% accuracy
+    path = os.path.join(os.path.dirname(__file__), "golden", "planck2018_sound_horizon.txt")
+    rows = np.loadtxt(path, comments="#", ndmin=2)
+    assert rows.shape == (2, 5)
+    for wb, wc, h, rd, _ in rows:
+        om = (wb + wc + P.OMEGA_NU) / h ** 2
+        assert abs(P.rd_aubourg(om, 100 * h, wb) - rd) < 0.1
 
 
 def test_projection_is_marginalisation_over_M():
