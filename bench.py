@@ -52,10 +52,11 @@ F_RHS_MW = 78
 F_ATT_FWD = 6 * F_RHS_MW + 2 * 6 * (21 + 7) + 40
 F_STEP_REV = 6 * F_RHS_MW + 2 * 6 * (15 + 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
 # DRAM bytes per accepted step of k_reverse_persist (fp32df, MW): ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch on 65,536 orbits (2.783 GB for 53.39M accepted steps), scaled by
-# the accepted steps of a launch. The tape slot is 48 bytes; the rest is chunk headers and outputs.
-# Valid for the kernel as profiled under profiles/mw_fp32df_reverse_k_reverse_persist.md only.
-REV_DRAM_BYTES_PER_STEP = 52.1
+# dram__bytes_write.sum of one full-size launch (1,048,576 orbits, 813.4 accepted steps each: 45.20 GB
+# read, 0.10 GB written), divided by its accepted steps. The tape slot is 48 bytes; the rest is chunk
+# headers and the per-orbit inputs and outputs. Valid for the kernel as profiled under
+# profiles/mw_fp32df_reverse_k_reverse_persist.md only.
+REV_DRAM_BYTES_PER_STEP = 53.1
 # FP32 ALU peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 1.25  # nominal GB300 FP64 rate
@@ -320,7 +321,7 @@ def run_gpu(args):
     achieved = flops / (dur / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic,
-                "traffic_note": "DRAM bytes per launch, from an ncu capture on 65,536 orbits scaled by accepted steps",
+                "traffic_note": "DRAM bytes per launch: bytes per accepted step from a one-pass ncu capture of the full-size launch, times this launch's accepted steps",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"}
 
     # ---------------- forward-only at the state budget ----------------
