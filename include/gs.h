@@ -161,8 +161,9 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
  *  recording gs_solve (status gains GS_ST_TAPE_OVERFLOW there); the forward solve is not re-run.
  *  The workspace holds the step tape: per accepted step the state at its start, its time and
  *  its length, in chunks taken from a pool by an atomic counter. Layout: a 256-byte header, int32
- *  head[N], n_rec[N] and order[N] (the reverse pass's longest-first order) and 4096 bucket counters
- *  (each array padded to 256 bytes), then chunks of 16 + 32 * slot bytes; a
+ *  head[N], n_rec[N] and order[N] (the longest-first work list), 4096 bucket counters and the
+ *  FP32 cost estimates cost[N] (each array padded to 256 bytes), then chunks of 16 + 32 * slot
+ *  bytes (a 16-byte header holding the previous chunk's index, then 32 slots); a
  *  trajectory with n accepted steps uses ceil(n / 32) chunks. slot = roundup16(state) + tail:
  *  GS_FP64 state 8 d bytes (FP64), tail 32 (t, tc, h, flag as FP64); GS_FP32_STAGES state 4 d (the
  *  FP32 high part, from which the stages are recomputed), tail 32; GS_FP32_DF state 4 d, tail 16
@@ -186,7 +187,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and caches
  * it: make that first call before any stream capture. Calls share the array and it keeps the last
  * call's contents (the call clears what must start at zero); calls that overlap on the GPU race, so
- * issue them one after another. N whose per-trajectory bookkeeping (12 N bytes, padded, plus the
+ * issue them one after another. N whose per-trajectory bookkeeping (16 N bytes, padded, plus the
  * 256-byte header, 16 KB of counters and one tape chunk) exceeds the array is rejected with
  * GS_ERR_WORKSPACE; trajectories whose
  * steps do not fit in the rest of the array get GS_ST_TAPE_OVERFLOW and NaN gradients. */

@@ -180,6 +180,7 @@ struct Traj {
   static constexpr int kSlotBytes = kTailOff + (DF ? 16 : 32);
   static_assert(kTailOff % 16 == 0 && kSlotBytes % 16 == 0 && kChunkHeader % 16 == 0,
                 "tape slots must stay 16-byte aligned");
+  static constexpr int kSlotWords = kSlotBytes / 4;
   static_assert(kStateBytes <= kTailOff, "state part of a slot overlaps its tail");
 
   T y[D];     // state (FP64) / high part (FP32), with its sensitivities when MT > 0
@@ -488,6 +489,45 @@ struct Traj {
     }
   }
 
+  // the words of the slot of the step just accepted (state at its start, padding, tail)
+  __device__ void slot_words(bool last, R hstep, uint32_t* w) const {
+    if constexpr (F32) {
+#pragma unroll
+      for (int i = 0; i < D; i++) w[i] = __float_as_uint(val(y[i]));
+    } else if constexpr (DD) {
+#pragma unroll
+      for (int i = 0; i < D; i++) { w[2 * i] = __float_as_uint(y[i].hi); w[2 * i + 1] = __float_as_uint(y[i].lo); }
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        const double v = val(y[i]);
+        w[2 * i] = uint32_t(__double2loint(v));
+        w[2 * i + 1] = uint32_t(__double2hiint(v));
+      }
+    }
+#pragma unroll
+    for (int i = kStateBytes / 4; i < kTailOff / 4; i++) w[i] = 0u;
+    constexpr int T0 = kTailOff / 4;
+    if constexpr (DF) {
+      w[T0] = __float_as_uint(th);
+      w[T0 + 1] = __float_as_uint(tl);
+      w[T0 + 2] = __float_as_uint(val(hstep));
+      w[T0 + 3] = __float_as_uint(last ? 1.0f : 0.0f);
+    } else {
+      const double tv[4] = {t, tc, h, last ? 1.0 : 0.0};
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        w[T0 + 2 * q] = uint32_t(__double2loint(tv[q]));
+        w[T0 + 2 * q + 1] = uint32_t(__double2hiint(tv[q]));
+      }
+    }
+  }
+  // A slot is written as kSlotBytes / 16 stores of 16 bytes, assembled in registers (state, zero
+  // padding, tail). Measured on the 2^20-orbit Milky-Way forward: 35.6 ms, against 38.3 ms for the
+  // same data written per field (three 8-byte stores for the six FP32 components, one for the tail),
+  // and against 38.3 ms for whole 32-byte sectors written in slot pairs through a shared-memory
+  // stash, although that removes the 34 GB of DRAM reads that completing partly written sectors
+  // costs: the stores are bound by issue, not by DRAM.
   __device__ void record_slot(const Problem& pb, bool last, R hstep) {
     if constexpr (MT == 0) {  // the tape is recorded by the solve without sensitivities
     const int a = nacc - 1;  // index of the step just accepted
@@ -501,38 +541,13 @@ struct Traj {
       hdr[0] = chunk;
       chunk = int32_t(idx);
     }
-    unsigned char* slot = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader +
-                          (long long)o * kSlotBytes;
-    if constexpr (F32) {
-      // vector stores: slots start 16-byte aligned (16-byte header, slots of multiples of 16 bytes)
-      if constexpr (D % 4 == 0) {
-        float4* f4 = reinterpret_cast<float4*>(slot);
+    // slots start 16-byte aligned (16-byte header, slots of multiples of 16 bytes)
+    uint4* s4 = reinterpret_cast<uint4*>(pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader +
+                                         (long long)o * kSlotBytes);
+    uint32_t w[kSlotWords];
+    slot_words(last, hstep, w);
 #pragma unroll
-        for (int q = 0; q < D / 4; q++) f4[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-      } else if constexpr (D % 2 == 0) {
-        float2* f2 = reinterpret_cast<float2*>(slot);
-#pragma unroll
-        for (int q = 0; q < D / 2; q++) f2[q] = make_float2(y[2 * q], y[2 * q + 1]);
-      } else {
-        float* f = reinterpret_cast<float*>(slot);
-#pragma unroll
-        for (int i = 0; i < D; i++) f[i] = y[i];
-      }
-    } else if constexpr (DD) {
-      float2* f2 = reinterpret_cast<float2*>(slot);  // (hi, lo) per component, 8-byte aligned
-#pragma unroll
-      for (int i = 0; i < D; i++) f2[i] = make_float2(y[i].hi, y[i].lo);
-    } else {
-      double* f = reinterpret_cast<double*>(slot);
-#pragma unroll
-      for (int i = 0; i < D; i++) f[i] = y[i];
-    }
-    if constexpr (DF) {
-      *reinterpret_cast<float4*>(slot + kTailOff) = make_float4(th, tl, val(hstep), last ? 1.0f : 0.0f);
-    } else {
-      double* tail = reinterpret_cast<double*>(slot + kTailOff);
-      tail[0] = t; tail[1] = tc; tail[2] = h; tail[3] = last ? 1.0 : 0.0;
-    }
+    for (int q = 0; q < kSlotWords / 4; q++) s4[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     }
   }
 
