@@ -116,6 +116,16 @@ def dist_env():
     return ws, rank, local
 
 
+def measured_hbm_gbs():
+    """The machine's measured HBM copy bandwidth (MEASURED_PEAKS.json beside this file), or None."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+
+
 # ------------------------------------------------------------------------------------------------
 def cpu_oracle_rate(e, rtol, target_s=15.0, nmax=200000, n=None):
     """The CPU oracle (FP64 same-algorithm solve + forward-sensitivity gradient) on a bounded sample
@@ -323,6 +333,12 @@ def run_gpu(args):
                 "frac": achieved / PEAK_FP32_TFLOPS, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch: bytes per accepted step from a one-pass ncu capture of the full-size launch, times this launch's accepted steps",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"}
+    if traffic is not None:
+        # the same launch's DRAM rate against the measured copy bandwidth: how far it is from HBM-bound
+        roofline["dram_gbs"] = traffic / (dur / 1e3) / 1e9
+        hbm = measured_hbm_gbs()
+        if hbm:
+            roofline["dram_frac_of_measured_hbm"] = roofline["dram_gbs"] / hbm
 
     # ---------------- forward-only at the state budget ----------------
     _, fwd_h, _ = make(HEAD_PREC, RTOL_FWD_F32)

@@ -136,6 +136,26 @@ def test_saved_stage_factors_match_recomputation(method, prec):
     assert np.all(np.isfinite(rel)) and np.percentile(rel, 99) < 1e-4 and rel.max() < 1e-3, (rel.max(), np.median(rel))
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32df"])
+@pytest.mark.parametrize("kernel", ["plain", "persistent"])
+def test_recording_does_not_change_the_solve(prec, kernel):
+    """A solve gives bit-identical states and step counts whether or not it records the tape, so a
+    tape sized from the accepted-step counts of an earlier plain solve always fits."""
+    ensure_built()
+    dev = torch.device("cuda")
+    e = W.mw(n=20000, seed=11, t1=750.0)
+    y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
+    t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
+    kw = dict(precision=prec, kernel=kernel)
+    s0 = api.solve("mw", y0, pr, t0, t1, sv, 1e-8, 1e-8, **kw)
+    nb = api.tape_bytes("mw", e.n, n_accept=s0["n_accept"], precision=prec)
+    s1 = api.solve("mw", y0, pr, t0, t1, sv, 1e-8, 1e-8, record_tape=True, workspace=api.Workspace(dev),
+                   tape_nbytes=nb, **kw)
+    assert int((s1["status"] != 0).sum()) == 0
+    assert torch.equal(s0["n_accept"], s1["n_accept"]) and torch.equal(s0["n_reject"], s1["n_reject"])
+    assert torch.equal(s0["y"], s1["y"])
+
+
 def test_adjoint_converges_to_oracle_gradient():
     """Discretisation: the FP64 adjoint at a tight tolerance against the oracle's converged
     forward-sensitivity gradient (Verner 7, rtol 1e-11)."""
