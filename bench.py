@@ -44,13 +44,30 @@ HEAD_PREC = "fp32df"
 
 # Algorithmic flops (sqrt, div, log counted as one op each), Tsit5 on the MW system:
 #   f:   ~70 add/mul + 4 sqrt + 1 log + 3 div = 78;  VJP of f: ~2.5 f = 195
-#   forward attempt: 6 f (FSAL) + 2d (nnz A + nnz(b - bhat)) = 2*6*(21+7) + ~40 controller = 880
+#   forward attempt: 6 f (FSAL) + 2d (nnz A + nnz(b - bhat)) + ~40 (error norm, controller)
+#                    = 468 + 2*6*(21+7) + 40 = 844
 #   reverse accepted step: the 6 stages the new state depends on (b_7 = 0): 6 f (k1 included)
 #                          + 2d (nnz of A among them + the 5 state updates) = 2*6*(15+5),
 #                          6 VJPs, and the cotangent algebra 2d (15 a_lj + 6 b_j) = 2130
 F_RHS_MW = 78
 F_ATT_FWD = 6 * F_RHS_MW + 2 * 6 * (21 + 7) + 40
 F_STEP_REV = 6 * F_RHS_MW + 2 * 6 * (15 + 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
+# Forward flops of the other workloads, the same count for any system and tableau: per attempt
+# (S - 1) f + 2d (nnz A + nnz(b - bhat)) + 40, plus 2d nnz b for the new state and one f per accepted
+# step (the next step's first stage) when the pair is not FSAL. f counts as written: MW 78, spin
+# precession 172 (after the per-binary constants), isochrone 14. Nonzeros of the published tableaux
+# (S, FSAL, nnz A, nnz b, nnz(b - bhat)):
+F_RHS = {"mw": 78, "precession": 172, "isochrone": 14}
+TABLEAU_NNZ = {"tsit5": (7, True, 21, 6, 7), "dopri5": (7, True, 20, 5, 6), "vern7": (10, False, 36, 7, 8)}
+
+
+def forward_flops(system, method, d, attempts, accepted):
+    S, fsal, n_a, n_b, n_e = TABLEAU_NNZ[method]
+    f = F_RHS[system]
+    per_attempt = (S - 1) * f + 2 * d * (n_a + (0 if fsal else n_b) + n_e) + 40
+    return attempts * per_attempt + (0 if fsal else accepted * f)
+
+
 # DRAM bytes per accepted step of k_reverse_persist (fp32df, MW): ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of one full-size launch (1,048,576 orbits, 813.4 accepted steps each: 45.20 GB
 # read, 0.10 GB written), divided by its accepted steps. The tape slot is 48 bytes; the rest is chunk
@@ -563,6 +580,14 @@ def run_workload(args):
                "fwd_solves_per_s": e.n / (f_ms / 1e3), "us_per_solve": 1e3 * f_ms / e.n, "p99_err": M.p99(er),
                "max_err": float(np.max(er)), "accepted": M.accepted(er, budget),
                "attempts_mean": float((s["n_accept"] + s["n_reject"]).double().mean())}
+        if system in F_RHS:
+            # achieved algorithmic flop rate of the forward against the ALU peak of its precision
+            att = float((s["n_accept"] + s["n_reject"]).double().sum())
+            acc = float(s["n_accept"].double().sum())
+            tf = forward_flops(system, meth, y0.shape[1], att, acc) / (f_ms / 1e3) / 1e12
+            peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+            row.update(fwd_tflops=tf, fwd_frac_of_peak=tf / peak, peak_kind="FP64 nominal" if prec == "fp64" else
+                       "FP32 derived")
         if grad:
             ws = api.Workspace(dev)
             nb = api.tape_bytes(system, e.n, n_accept=s["n_accept"], precision=prec)
@@ -853,7 +878,8 @@ def run_case(args):
     """Small profiling cases of the headline kernels (no JSON line): the seeded MW workload with
     --n orbits at --rtol, solved twice. 'fwd': persistent forward without a tape; 'fwdrev': forward
     recording its tape, then the persistent reverse sweep. --t1-myr shortens the orbits so that a
-    case with several trajectories per lane keeps its tape to a few GB."""
+    case with several trajectories per lane keeps its tape to a few GB. 'prec': --n spin-precession
+    solves, FP64 Verner 7 persistent forward."""
     import torch
 
     from paper_2609_28458_gb300 import api
@@ -862,6 +888,17 @@ def run_case(args):
 
     gsbuild.build()
     dev = torch.device("cuda")
+    if args.case == "prec":  # spin precession, FP64 Verner 7, persistent forward (the workload's kernel)
+        p = W.precession(n=args.n, seed=2000)
+        py0, pp = torch.as_tensor(p.y0, device=dev), torch.as_tensor(p.params, device=dev)
+        pt0, pt1, psv = (torch.as_tensor(x, device=dev) for x in (p.t0, p.t1, p.saveat))
+        for _ in range(2):
+            s = api.solve("precession", py0, pp, pt0, pt1, psv, 3.16e-9, 3.16e-9, method="vern7", precision="fp64",
+                          kernel="persistent")
+        torch.cuda.synchronize()
+        log("case prec: n=%d status!=0 %d mean attempts %.1f" % (args.n, int((s["status"] != 0).sum()),
+                                                                 float((s["n_accept"] + s["n_reject"]).double().mean())))
+        return
     e = W.mw(n=args.n, seed=1000, t1=args.t1_myr)
     y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
     t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
@@ -892,7 +929,7 @@ def main():
     ap.add_argument("--acc-sample", type=int, default=16384)
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--case", choices=["fwd", "fwdrev"], help="run a small profiling case instead")
+    ap.add_argument("--case", choices=["fwd", "fwdrev", "prec"], help="run a small profiling case instead")
     ap.add_argument("--t1-myr", type=float, default=T1_MYR, help="orbit length of a --case run")
     ap.add_argument("--workload", default="mw",
                     choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "quintessence_flat",
