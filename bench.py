@@ -581,13 +581,15 @@ def run_workload(args):
                "max_err": float(np.max(er)), "accepted": M.accepted(er, budget),
                "attempts_mean": float((s["n_accept"] + s["n_reject"]).double().mean())}
         if system in F_RHS:
-            # achieved algorithmic flop rate of the forward against the ALU peak of its precision
+            # achieved algorithmic flop rate of the forward against the ALU peak of its precision (none
+            # for df64, whose every operation is a sequence of FP32 instructions)
             att = float((s["n_accept"] + s["n_reject"]).double().sum())
             acc = float(s["n_accept"].double().sum())
             tf = forward_flops(system, meth, y0.shape[1], att, acc) / (f_ms / 1e3) / 1e12
-            peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
-            row.update(fwd_tflops=tf, fwd_frac_of_peak=tf / peak, peak_kind="FP64 nominal" if prec == "fp64" else
-                       "FP32 derived")
+            row["fwd_tflops"] = tf
+            if prec != "df64":
+                peak = PEAK_FP64_TFLOPS if prec == "fp64" else PEAK_FP32_TFLOPS
+                row.update(fwd_frac_of_peak=tf / peak, peak_kind="FP64 nominal" if prec == "fp64" else "FP32 derived")
         if grad:
             ws = api.Workspace(dev)
             nb = api.tape_bytes(system, e.n, n_accept=s["n_accept"], precision=prec)
