@@ -28,7 +28,7 @@ struct LaunchCfg {
 // Resident 128-thread blocks per SM requested from the register allocator (__launch_bounds__), for
 // 7-stage pairs on states of at most 6 components: the FP32-pipe forward 4 blocks (128 registers;
 // measured on the 3 Gyr Milky-Way ensemble, 5 blocks at 96 registers is 11% slower and 6 blocks 42%),
-// the FP64-control forward 4, the FP32 reverse 3 (<= 168; 2 blocks is 15% slower, 4 blocks 4%), without
+// the FP64-control forward 4, the FP32 reverse 3 (<= 168; 2 blocks is 15% slower, 4 blocks 5%), without
 // spills. FP64, Verner 7 and the 9-component precession state keep the compiler's choice.
 #ifndef GS_FWD_BLOCKS_FP32DF
 #define GS_FWD_BLOCKS_FP32DF 4
@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(128) k_reverse(const Problem pb) {
 }
 
 // Shared memory of the persistent reverse pass per thread: the stage Jacobian factors (FP32 modes
-// of systems with f_save, 7-stage pairs), S x SaveQ float4 = 336 bytes for the Milky-Way system,
-// 43 KB per 128-thread block.
+// of systems with f_save, 7-stage pairs), S x SaveQ float4 = 224 bytes for the Milky-Way system,
+// 28.7 KB per 128-thread block.
 template <template <class> class SysT, class Tab, int PM>
 struct RevSlab {
   static constexpr int Q = SaveQ<SysT<float>>::value;
