@@ -26,12 +26,13 @@ struct LaunchCfg {
 };
 
 // Resident 128-thread blocks per SM requested from the register allocator (__launch_bounds__), for
-// 7-stage pairs on states of at most 6 components: the FP32-pipe forward 4 blocks (128 registers;
-// measured on the 3 Gyr Milky-Way ensemble, 5 blocks at 96 registers is 11% slower and 6 blocks 42%),
-// the FP64-control forward 4, the FP32 reverse 3 (<= 168; 2 blocks is 15% slower, 4 blocks 5%), without
-// spills. FP64, Verner 7 and the 9-component precession state keep the compiler's choice.
+// 7-stage pairs on states of at most 6 components: the FP32-pipe forward 5 blocks (96 registers and a
+// few spilled; measured on the 3 Gyr Milky-Way ensemble against 4 blocks at 128 registers: 1% faster
+// with the tape, 2% without; 6 blocks 42% slower), the FP64-control forward 4, the FP32 reverse 3
+// (<= 168; 2 blocks is 15% slower, 4 blocks 5%), without spills. FP64, Verner 7 and the 9-component
+// precession state keep the compiler's choice.
 #ifndef GS_FWD_BLOCKS_FP32DF
-#define GS_FWD_BLOCKS_FP32DF 4
+#define GS_FWD_BLOCKS_FP32DF 5
 #endif
 #ifndef GS_REV_BLOCKS_FP32
 #define GS_REV_BLOCKS_FP32 3
