@@ -5,7 +5,8 @@
   apocentre radius at T_r / 2 from the radial energy equation;
 * measured convergence orders of every tableau and of the dense output on that closed form;
 * conserved quantities: energy and angular momentum of the orbit systems (Sec. 3); unit lengths,
-  effective spin and total angular momentum of the precession equations (Sec. 5); Lambda-CDM
+  effective spin and total angular momentum of the precession equations (Sec. 5), and their
+  radiation reaction for non-spinning binaries from the 2PN energy balance; Lambda-CDM
   distances by Gauss-Legendre quadrature at lambda = 0, and the decrease of rho_phi (Eq. de-rho)
   and w >= -1 (Eq. de-w) for lambda > 0 (Sec. 4, Appendix C);
 * the exactness statement of Sec. 2.3 / Eq. stage-sens: forward sensitivities on a fixed step
@@ -220,6 +221,43 @@ def test_precession_rhs_identities():
         assert abs(dxi) < 1e-13 * scale
         dJ = (eta / v) * fL + S1 * f1 + S2 * f2  # dJ/dv + eta/v^2 Lhat
         assert np.max(np.abs(dJ)) < 1e-13 * scale * max(S1 + S2 + eta / v, 1.0)
+
+
+def _series_div(num, den, order):
+    """Coefficients c_0..c_order of num(x) / den(x) for power series with den[0] = 1."""
+    c = []
+    for n in range(order + 1):
+        c.append((num[n] if n < len(num) else 0.0) - sum(den[k] * c[n - k] for k in range(1, min(n, len(den) - 1) + 1)))
+    return c
+
+
+def test_precession_radiation_reaction_matches_energy_balance():
+    """Pin of the radiation-reaction coefficients b_2, b_3, b_4 (Sec. 5, Eq. prec-rr) for non-spinning
+    binaries, derived here independently: dv/dt = -F(v) / (dE/dv) from the 2PN binding energy
+    E(v) = -(eta v^2 / 2) [1 - (3/4 + eta/12) v^2 - (27/8 - 19/8 eta + eta^2/24) v^4] and the 2PN
+    flux F(v) = 32/5 eta^2 v^10 [1 - (1247/336 + 35/12 eta) v^2 + 4 pi v^3
+    + (-44711/9072 + 9271/504 eta + 65/18 eta^2) v^4] of point masses (Blanchet, Living Rev.
+    Relativ. 17, 2 (2014)), by series division. With chi1 = chi2 = 0 the spin S1hat precesses about
+    Lhat at Omega_1 = (2 + 3q/2) eta v^5 (Eq. prec-omega with no spin terms), so the oracle's dv/dt is
+    |Omega_1 x S1hat| / |dS1hat/dv|. A wrong numerator or denominator in b_2 or b_4, or a dropped
+    v^3 tail term, shows up far above 1e-12."""
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        q = rng.uniform(0.1, 1.0)
+        v = rng.uniform(0.05, 0.35)
+        eta = q / (1 + q) ** 2
+        e2 = -(0.75 + eta / 12)
+        e4 = -(27 / 8 - 19 / 8 * eta + eta ** 2 / 24)
+        dE = [1.0, 0.0, 2 * e2, 0.0, 3 * e4]                 # (dE/dv) / (-eta v)
+        flux = [1.0, 0.0, -(1247 / 336 + 35 / 12 * eta), 4 * np.pi, -44711 / 9072 + 9271 / 504 * eta + 65 / 18 * eta ** 2]
+        c = _series_div(flux, dE, 4)
+        dvdt_2pn = 32 / 5 * eta * v ** 9 * sum(c[k] * v ** k for k in range(5))
+        vecs = [u / np.linalg.norm(u) for u in rng.normal(size=(3, 3))]
+        y = np.concatenate(vecs)
+        f = O.rhs("precession", v, y, np.array([q, 0.0, 0.0]))
+        omega1 = (2 + 1.5 * q) * eta * v ** 5 * vecs[0]
+        dvdt_oracle = np.linalg.norm(np.cross(omega1, vecs[1])) / np.linalg.norm(f[3:6])
+        assert abs(dvdt_oracle / dvdt_2pn - 1) < 1e-12, (q, v, dvdt_oracle, dvdt_2pn)
 
 
 def test_precession_solve_invariants():
