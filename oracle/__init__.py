@@ -92,6 +92,17 @@ def rhs(system, t, y, p=None):
     return f
 
 
+def initial_step(system, method, t0, t1, y0, p=None, rtol=1e-6, atol=1e-6):
+    """The starting step a solve of `method` takes from (t0, y0) towards t1 (HNW I, Sec. II.4)."""
+    d, np_ = dims(system)
+    y0 = np.ascontiguousarray(y0, dtype=np.float64)
+    p = np.ascontiguousarray(p if p is not None else np.zeros(max(np_, 1)), dtype=np.float64)
+    f = lib().orc_initial_step
+    f.restype = ctypes.c_double
+    return f(_sys(system), _meth(method), ctypes.c_double(t0), ctypes.c_double(t1), _p(y0), _p(p),
+             ctypes.c_double(rtol), ctypes.c_double(atol))
+
+
 def jvp(system, t, y, p, vy, vp=None):
     d, np_ = dims(system)
     y = np.ascontiguousarray(y, dtype=np.float64)

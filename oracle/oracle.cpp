@@ -27,9 +27,9 @@
 // Parity pins: the tableaux are checked against the Butcher order conditions and measured
 // convergence orders; whole solves against isochrone closed forms, conserved quantities of
 // every system, and Lambda-CDM distances by quadrature; the forward sensitivities against
-// central finite differences of the fixed-step replay. The initial-step heuristic has no
-// independent pin of its own (parity unpinned for that function alone): it is deterministic and
-// the solves that use it are pinned as a whole.
+// central finite differences of the fixed-step replay; the starting step against SciPy's
+// implementation of the same published algorithm. The spin terms of the precession radiation
+// reaction are parity unpinned (see systems.hpp).
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
@@ -412,6 +412,18 @@ int orc_dense_weights(int method, double sigma, double* w) { return dense_weight
 int orc_rhs(int sys, double t, const double* y, const double* p, double* f) {
   rhs<double>(sys, t, y, p, f);
   return 0;
+}
+
+// The starting step every solve of `method` takes from (t0, y0) towards t1 (Hairer, Norsett &
+// Wanner I, Sec. II.4, with p the method's order), exposed so that tests can compare it with an
+// independent implementation of that algorithm.
+double orc_initial_step(int sys, int method, double t0, double t1, const double* y0, const double* p, double rtol,
+                        double atol) {
+  int d, np;
+  dims(sys, &d, &np);
+  double f0[9];
+  rhs<double>(sys, t0, y0, p, f0);
+  return initial_step(sys, get_tableau(method).order, t0, t1, y0, p, f0, rtol, atol, d);
 }
 
 // J_y vy + J_theta vp at (t, y, theta), by one forward-mode pass.

@@ -12,6 +12,7 @@
 * the exactness statement of Sec. 2.3 / Eq. stage-sens: forward sensitivities on a fixed step
   sequence equal the derivative of the discrete solution (central differences of the replay);
 * the converged-reference check of Appendix A / Appendix D (10x looser tolerance within eps_req/10);
+* the starting step against SciPy's implementation of the same published algorithm;
 * the failure conventions (status codes, NaN outputs).
 """
 import numpy as np
@@ -258,6 +259,33 @@ def test_precession_radiation_reaction_matches_energy_balance():
         omega1 = (2 + 1.5 * q) * eta * v ** 5 * vecs[0]
         dvdt_oracle = np.linalg.norm(np.cross(omega1, vecs[1])) / np.linalg.norm(f[3:6])
         assert abs(dvdt_oracle / dvdt_2pn - 1) < 1e-12, (q, v, dvdt_oracle, dvdt_2pn)
+
+
+@pytest.mark.parametrize("method,order", [("tsit5", 5), ("dopri5", 5), ("vern7", 7)])
+def test_starting_step_matches_library_routine(method, order):
+    """The oracle's starting step (Hairer, Norsett & Wanner I, Sec. II.4; p = the method's order, our
+    reading) equals SciPy's implementation of the same published algorithm, called with the oracle's
+    right-hand side, on members of every workload."""
+    common = pytest.importorskip("scipy.integrate._ivp.common")
+    gens = [("isochrone", W.isochrone(n=6, seed=71)), ("mw", W.mw(n=6, seed=72)),
+            ("precession", W.precession(n=6, seed=73, paper_interval=True)),
+            ("quintessence", W.quintessence(n=6, seed=74, rtol=1e-6)), ("loghalo", W.loghalo(n=6, seed=75))]
+    for system, e in gens:
+        for i in range(e.n):
+            p = e.params[i] if e.params.shape[1] else None
+            t0, t1 = float(np.ravel(e.t0)[i]), float(np.ravel(e.t1)[i])
+            rtol, atol = 1e-7, 1e-9
+
+            def fun(t, y):
+                return O.rhs(system, t, y, p)
+
+            f0 = fun(t0, e.y0[i])
+            try:
+                ref = common.select_initial_step(fun, t0, e.y0[i], t1, np.inf, f0, 1.0, order, rtol, atol)
+            except TypeError:  # older SciPy signature without t_bound and max_step
+                ref = min(common.select_initial_step(fun, t0, e.y0[i], f0, 1.0, order, rtol, atol), t1 - t0)
+            h = O.initial_step(system, method, t0, t1, e.y0[i], p, rtol, atol)
+            assert abs(h - ref) <= 1e-12 * ref, (system, i, h, ref)
 
 
 def test_precession_solve_invariants():
