@@ -28,8 +28,8 @@
 // convergence orders; whole solves against isochrone closed forms, conserved quantities of
 // every system, and Lambda-CDM distances by quadrature; the forward sensitivities against
 // central finite differences of the fixed-step replay; the starting step against SciPy's
-// implementation of the same published algorithm. The spin terms of the precession radiation
-// reaction are parity unpinned (see systems.hpp).
+// implementation of the same published algorithm; the precession radiation reaction against the
+// 2PN energy balance.
 #include <cfloat>
 #include <cmath>
 #include <cstdint>

@@ -93,8 +93,8 @@ void rhs_orbit(int sys, const T* y, const T* p, int np, T* f) {
 // (Sec. 5, Eqs. prec-spins, prec-L, prec-omega, prec-rr). State y = (Lhat, S1hat, S2hat),
 // theta = (q, chi1, chi2). The radiation-reaction coefficients b_k are not printed in the
 // paper; here b_2, b_3, b_4 are the 2PN spin-orbit and spin-spin flux terms of Kidder (1995),
-// the work the paper cites for these equations, and b_5..b_7 = 0. Their non-spinning parts are
-// pinned by the 2PN energy balance (tests); the spin terms are parity unpinned.
+// the work the paper cites for these equations, and b_5..b_7 = 0. They are pinned by the 2PN
+// energy balance -F / (dE/dv) of the published binding energy and flux (tests).
 template <class T>
 void cross3(const T a[3], const T b[3], T r[3]) {
   r[0] = a[1] * b[2] - a[2] * b[1];

@@ -6,7 +6,7 @@
 * measured convergence orders of every tableau and of the dense output on that closed form;
 * conserved quantities: energy and angular momentum of the orbit systems (Sec. 3); unit lengths,
   effective spin and total angular momentum of the precession equations (Sec. 5), and their
-  radiation reaction for non-spinning binaries from the 2PN energy balance; Lambda-CDM
+  radiation reaction from the 2PN energy balance (spin-orbit and spin-spin terms included); Lambda-CDM
   distances by Gauss-Legendre quadrature at lambda = 0, and the decrease of rho_phi (Eq. de-rho)
   and w >= -1 (Eq. de-w) for lambda > 0 (Sec. 4, Appendix C);
 * the exactness statement of Sec. 2.3 / Eq. stage-sens: forward sensitivities on a fixed step
@@ -233,32 +233,44 @@ def _series_div(num, den, order):
 
 
 def test_precession_radiation_reaction_matches_energy_balance():
-    """Pin of the radiation-reaction coefficients b_2, b_3, b_4 (Sec. 5, Eq. prec-rr) for non-spinning
-    binaries, derived here independently: dv/dt = -F(v) / (dE/dv) from the 2PN binding energy
-    E(v) = -(eta v^2 / 2) [1 - (3/4 + eta/12) v^2 - (27/8 - 19/8 eta + eta^2/24) v^4] and the 2PN
-    flux F(v) = 32/5 eta^2 v^10 [1 - (1247/336 + 35/12 eta) v^2 + 4 pi v^3
-    + (-44711/9072 + 9271/504 eta + 65/18 eta^2) v^4] of point masses (Blanchet, Living Rev.
-    Relativ. 17, 2 (2014)), by series division. With chi1 = chi2 = 0 the spin S1hat precesses about
-    Lhat at Omega_1 = (2 + 3q/2) eta v^5 (Eq. prec-omega with no spin terms), so the oracle's dv/dt is
-    |Omega_1 x S1hat| / |dS1hat/dv|. A wrong numerator or denominator in b_2 or b_4, or a dropped
-    v^3 tail term, shows up far above 1e-12."""
+    """Pin of the radiation-reaction coefficients b_2, b_3, b_4 (Sec. 5, Eq. prec-rr), derived here
+    independently as dv/dt = -F(v) / (dE/dv) by series division of the 2PN binding energy and
+    gravitational-wave flux, with l_j = Lhat.S_jhat, s_12 = S_1hat.S_2hat, m_1 = 1/(1+q), m_2 = q m_1:
+      E = -(eta v^2/2) [1 - (3/4 + eta/12) v^2 + sum_j (8/3 m_j^2 + 2 eta) chi_j l_j v^3
+          - (27/8 - 19/8 eta + eta^2/24) v^4 + eta chi_1 chi_2 (s_12 - 3 l_1 l_2) v^4],
+      F = 32/5 eta^2 v^10 [1 - (1247/336 + 35/12 eta) v^2 + (4 pi - sum_j (11/4 m_j^2 + 5/4 eta)
+          chi_j l_j) v^3 + (-44711/9072 + 9271/504 eta + 65/18 eta^2) v^4
+          + eta/48 chi_1 chi_2 (-103 s_12 + 289 l_1 l_2) v^4]
+    (point masses: Blanchet, Living Rev. Relativ. 17, 2 (2014); spin-orbit and spin-spin terms:
+    Kidder, Phys. Rev. D 52, 821 (1995)). The oracle's dv/dt is read off the precession of S1hat:
+    dS1hat/dt = Omega_1 x S1hat with Omega_1 = v^6/2 [(4 + 3q)(eta/v) Lhat + S_2 S2hat
+    - 3 (S_2 l_2 + q S_1 l_1) Lhat], S_j = chi_j m_j^2 (Eq. prec-omega), so dv/dt = |Omega_1 x S1hat| /
+    |dS1hat/dv|. A wrong
+    coefficient in any b_k, or a dropped spin term, shows up far above 1e-12."""
     rng = np.random.default_rng(4)
-    for _ in range(40):
+    for _ in range(60):
         q = rng.uniform(0.1, 1.0)
+        chi1, chi2 = (0.0, 0.0) if _ < 10 else tuple(rng.uniform(0, 1, 2))
         v = rng.uniform(0.05, 0.35)
-        eta = q / (1 + q) ** 2
+        m1 = 1 / (1 + q)
+        m2 = q * m1
+        eta = m1 * m2
+        Lh, s1, s2 = [u / np.linalg.norm(u) for u in rng.normal(size=(3, 3))]
+        l1, l2, s12 = Lh @ s1, Lh @ s2, s1 @ s2
+        so_e = (8 / 3 * m1 ** 2 + 2 * eta) * chi1 * l1 + (8 / 3 * m2 ** 2 + 2 * eta) * chi2 * l2
+        so_f = (11 / 4 * m1 ** 2 + 5 / 4 * eta) * chi1 * l1 + (11 / 4 * m2 ** 2 + 5 / 4 * eta) * chi2 * l2
         e2 = -(0.75 + eta / 12)
-        e4 = -(27 / 8 - 19 / 8 * eta + eta ** 2 / 24)
-        dE = [1.0, 0.0, 2 * e2, 0.0, 3 * e4]                 # (dE/dv) / (-eta v)
-        flux = [1.0, 0.0, -(1247 / 336 + 35 / 12 * eta), 4 * np.pi, -44711 / 9072 + 9271 / 504 * eta + 65 / 18 * eta ** 2]
+        e4 = -(27 / 8 - 19 / 8 * eta + eta ** 2 / 24) + eta * chi1 * chi2 * (s12 - 3 * l1 * l2)
+        dE = [1.0, 0.0, 2 * e2, 2.5 * so_e, 3 * e4]          # (dE/dv) / (-eta v)
+        flux = [1.0, 0.0, -(1247 / 336 + 35 / 12 * eta), 4 * np.pi - so_f,
+                -44711 / 9072 + 9271 / 504 * eta + 65 / 18 * eta ** 2 + eta / 48 * chi1 * chi2 * (-103 * s12 + 289 * l1 * l2)]
         c = _series_div(flux, dE, 4)
         dvdt_2pn = 32 / 5 * eta * v ** 9 * sum(c[k] * v ** k for k in range(5))
-        vecs = [u / np.linalg.norm(u) for u in rng.normal(size=(3, 3))]
-        y = np.concatenate(vecs)
-        f = O.rhs("precession", v, y, np.array([q, 0.0, 0.0]))
-        omega1 = (2 + 1.5 * q) * eta * v ** 5 * vecs[0]
-        dvdt_oracle = np.linalg.norm(np.cross(omega1, vecs[1])) / np.linalg.norm(f[3:6])
-        assert abs(dvdt_oracle / dvdt_2pn - 1) < 1e-12, (q, v, dvdt_oracle, dvdt_2pn)
+        f = O.rhs("precession", v, np.concatenate([Lh, s1, s2]), np.array([q, chi1, chi2]))
+        S1, S2 = chi1 * m1 ** 2, chi2 * m2 ** 2
+        omega1 = v ** 6 / 2 * ((4 + 3 * q) * (eta / v) * Lh + S2 * s2 - 3 * (S2 * l2 + q * S1 * l1) * Lh)
+        dvdt_oracle = np.linalg.norm(np.cross(omega1, s1)) / np.linalg.norm(f[3:6])
+        assert abs(dvdt_oracle / dvdt_2pn - 1) < 1e-12, (q, chi1, chi2, v, dvdt_oracle, dvdt_2pn)
 
 
 @pytest.mark.parametrize("method,order", [("tsit5", 5), ("dopri5", 5), ("vern7", 7)])
