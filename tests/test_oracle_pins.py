@@ -4,6 +4,7 @@
   period pi (1 + L / sqrt(L^2 + 4)) (Binney & Tremaine, the textbook the paper cites in Sec. 3);
   apocentre radius at T_r / 2 from the radial energy equation;
 * measured convergence orders of every tableau and of the dense output on that closed form;
+* Poisson's equation for every potential component against the densities that generate them;
 * conserved quantities: energy and angular momentum of the orbit systems (Sec. 3); unit lengths,
   effective spin and total angular momentum of the precession equations (Sec. 5), and their
   radiation reaction from the 2PN energy balance (spin-orbit and spin-spin terms included); Lambda-CDM
@@ -200,6 +201,47 @@ def _prec_quantities(y, p):
     L, s1, s2 = y[..., 0:3], y[..., 3:6], y[..., 6:9]
     xi = ((1 + q) * S1)[..., None] * s1 + ((1 + 1 / q) * S2)[..., None] * s2
     return L, s1, s2, (xi * L).sum(-1), S1, S2, m1 * m2
+
+
+def _laplacian(system, x, p, h=1e-3):
+    c = O.potential(system, x, p)
+    acc = 0.0
+    for i in range(3):
+        dx = np.zeros(3)
+        dx[i] = h
+        acc += O.potential(system, x + dx, p) - 2 * c + O.potential(system, x - dx, p)
+    return acc / h ** 2
+
+
+def test_potentials_satisfy_poisson_with_textbook_densities():
+    """Poisson's equation, Laplacian(Phi) = 4 pi G rho, for each component of the Milky-Way potential
+    (Sec. 3) and for the logarithmic halo (Eq. loghalo), with the densities that generate them
+    written from Binney & Tremaine (2008): Miyamoto-Nagai rho = b^2 M [a R^2 + (a + 3 zeta)(a +
+    zeta)^2] / (4 pi [R^2 + (a + zeta)^2]^(5/2) zeta^3), zeta^2 = z^2 + b^2; Hernquist rho = M c /
+    (2 pi r (r + c)^3); NFW rho = M_h / (4 pi r (r_s + r)^2); logarithmic halo 4 pi G rho = (v_c^2 /
+    q^2) [(2 q^2 + 1) R_c^2 + R^2 + (2 - 1/q^2) z^2] / (R_c^2 + R^2 + z^2/q^2)^2. G in kpc^3 /
+    (1e10 Msun Myr^2) from the IAU solar mass parameter; Laplacian by central differences."""
+    G = 1e10 * 1.3271244e20 * 3.15576e13 ** 2 / 3.0856775814913673e19 ** 3
+    a, b, c, rs = 3.0, 0.28, 1.0, 15.6
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        R, phi, z = rng.uniform(1.0, 20.0), rng.uniform(0, 2 * np.pi), rng.uniform(-3.0, 3.0)
+        x = np.array([R * np.cos(phi), R * np.sin(phi), z])
+        r = np.linalg.norm(x)
+        zeta = np.sqrt(z * z + b * b)
+        M = 6.8
+        rho_d = b * b * M * (a * R * R + (a + 3 * zeta) * (a + zeta) ** 2) / (
+            4 * np.pi * (R * R + (a + zeta) ** 2) ** 2.5 * zeta ** 3)
+        rho_b = 0.5 * c / (2 * np.pi * r * (r + c) ** 3)
+        rho_h = 54.0 / (4 * np.pi * r * (rs + r) ** 2)
+        for pv, rho in (([M, 0, 0, 1.0], rho_d), ([0, 0.5, 0, 1.0], rho_b), ([0, 0, 54.0, 1.0], rho_h)):
+            lap = _laplacian("mw", x, np.array(pv, dtype=float))
+            assert abs(lap / (4 * np.pi * G * rho) - 1) < 1e-5, (pv, lap, 4 * np.pi * G * rho)
+        vc, Rc, q = 1.0, 0.2, rng.uniform(0.6, 1.0)
+        Q = Rc * Rc + R * R + z * z / q ** 2
+        lap_log = vc * vc / q ** 2 * ((2 * q * q + 1) * Rc * Rc + R * R + (2 - 1 / q ** 2) * z * z) / Q ** 2
+        lap = _laplacian("loghalo", x, np.array([vc, Rc, q]))
+        assert abs(lap / lap_log - 1) < 1e-5, (lap, lap_log)
 
 
 def test_precession_rhs_identities():
