@@ -244,6 +244,27 @@ def test_potentials_satisfy_poisson_with_textbook_densities():
         assert abs(lap / lap_log - 1) < 1e-5, (lap, lap_log)
 
 
+def test_quintessence_field_equation_preserves_the_friedmann_constraint():
+    """Along the flow the constraint E^2 (1 - u^2/6) = Om e^-3N + Or e^-4N + a0 e^-lam phi (Eq. de-model)
+    must stay consistent with dlnE/dN = -(3 Om e^-3N + 4 Or e^-4N)/(2 E^2) - u^2/2: the total
+    N-derivative of E^2 through phi' = u and the oracle's u' (the scalar-field equation of Eq.
+    de-rhs) equals 2 E^2 dlnE/dN (the Bianchi identity). A wrong factor in u' breaks it."""
+    rng = np.random.default_rng(12)
+    for _ in range(50):
+        N = rng.uniform(-3.9, 0.0)
+        phi, u = rng.uniform(0, 0.6), rng.uniform(-0.8, 0.8)
+        a0, lam, om, orad = rng.uniform(0.6, 0.75), rng.uniform(0, 1.5), rng.uniform(0.28, 0.34), 9e-5
+        f = O.rhs("quintessence", N, np.array([phi, u, 0.0]), np.array([a0, lam, om, orad]))
+        A, B, V = om * np.exp(-3 * N), orad * np.exp(-4 * N), a0 * np.exp(-lam * phi)
+        D = 1 - u * u / 6
+        E2 = (A + B + V) / D
+        dE2 = (-3 * A - 4 * B) / D + f[0] * (-lam * V / D) + f[1] * E2 * (u / 3) / D
+        dlnE = -(3 * A + 4 * B) / (2 * E2) - u * u / 2
+        assert abs(f[0] - u) < 1e-15
+        assert abs(dE2 - 2 * E2 * dlnE) < 1e-12 * (abs(2 * E2 * dlnE) + E2), (dE2, 2 * E2 * dlnE)
+        assert abs(f[2] - np.exp(-N) / np.sqrt(E2)) < 1e-14 * abs(f[2])
+
+
 def test_precession_rhs_identities():
     """At random states: |Lhat|, |S_jhat| fixed (Eq. prec-spins, prec-L), effective spin fixed, and
     the total angular momentum J = (eta/v) Lhat + S1 + S2 changes only through L: dJ/dv = -eta/v^2 Lhat
