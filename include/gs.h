@@ -196,7 +196,9 @@ int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* pa
                    const gs_options* opt, const double* dLdy, double* dLdy0, double* dLdparams,
                    double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* cuda_stream);
 
-/* Workspace bytes for N trajectories. for_vjp = 0: the persistent kernel's counter only.
+/* Workspace bytes for N trajectories. for_vjp = 0: the work counters and the longest-first work
+ * list (order[N], bucket counters, cost[N]); a smaller workspace runs GS_ORDER_AUTO in stored order
+ * and rejects GS_ORDER_ESTIMATE and GS_ORDER_HINT with GS_ERR_WORKSPACE.
  * for_vjp != 0: room for a step tape of `steps_hint` accepted steps per trajectory on average
  * (rounded up to whole chunks per trajectory, plus one), in the slot size of opt->precision
  * (FP64 when opt is NULL). A smaller workspace is accepted; trajectories whose steps no longer

@@ -83,7 +83,12 @@ int set_order(gs::Problem& pb, const gs_options* opt, int64_t N, void* ws, size_
   bool use = false;
   if (opt->order == GS_ORDER_HINT || opt->order == GS_ORDER_ESTIMATE) use = true;
   if (opt->order == GS_ORDER_AUTO) use = opt->cost_hint != nullptr || N >= 32768;
-  if (!use || !ws || ws_bytes < L.total_fixed) return GS_OK;  // as stored
+  if (!use) return GS_OK;
+  if (!ws || ws_bytes < L.total_fixed) {
+    if (opt->order == GS_ORDER_AUTO) return GS_OK;  // as stored
+    return fail(GS_ERR_WORKSPACE, "a longest-first order needs a workspace of gs_workspace_bytes(..., for_vjp = 0) "
+                "= %zu bytes", L.total_fixed);
+  }
   unsigned char* base = static_cast<unsigned char*>(ws);
   pb.cost_hint = (opt->order == GS_ORDER_ESTIMATE) ? nullptr : opt->cost_hint;
   pb.ord_cost = reinterpret_cast<float*>(base + L.cost);
@@ -277,12 +282,12 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     if (rc) return rc;
     pb.record = 1;
   }
+  rc = set_order(pb, opt, N, workspace, workspace_bytes);
+  if (rc) return rc;
   if (need_ws) {
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   }
-  rc = set_order(pb, opt, N, workspace, workspace_bytes);
-  if (rc) return rc;
   gs::LaunchCfg c{opt->method, opt->precision, kernel, opt->block_size, s, opt->sm_limit};
   cudaError_t e = forward_of(system, opt->method)(pb, c);
   if (e != cudaSuccess) return cuda_fail(e, "forward launch");

@@ -110,7 +110,8 @@ def test_solve_flat_argument_checks(lib):
 
 
 def test_order_option_checks(lib):
-    """gs_options.order: unknown values and GS_ORDER_HINT without a hint are rejected on the host."""
+    """gs_options.order: unknown values, GS_ORDER_HINT without a hint and an explicit order without a
+    workspace are rejected on the host."""
     fake = ctypes.c_void_p(256)
     for order, hint in ((7, None), (-1, None), (_abi.ORDERS["hint"], None)):
         o = _abi.options(kernel="plain", order=order)
@@ -119,4 +120,10 @@ def test_order_option_checks(lib):
         rc = lib.gs_solve(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
                           None, 0, None)
         assert rc == _abi.GS_ERR_INVALID, order
+    # an explicit longest-first order without room for the work list fails; AUTO falls back to the
+    # stored order (both before any device work)
+    o = _abi.options(kernel="plain", order="estimate")
+    rc = lib.gs_solve(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
+                      None, 0, None)
+    assert rc == _abi.GS_ERR_WORKSPACE
     assert ctypes.sizeof(_abi.GsOptions) == 104
