@@ -453,9 +453,11 @@ def run_gpu(args):
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 (stages) + f32-pair time", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "mw_1048576_orbits_0_3gyr", "N_per_gpu": N, "system": "mw", "method": "tsit5",
-                       "precision": HEAD_PREC, "kernel": "persistent forward (tape) + persistent reverse",
+                       "precision": HEAD_PREC,
+                       "arithmetic": "FP32 stages and controller; state and time as compensated FP32 pairs",
+                       "kernel": "persistent forward (tape) + persistent reverse",
                        "rtol": RTOL_GRAD, "atol": RTOL_GRAD, "t1_myr": T1_MYR,
                        "budgets": {"orbit_p99": BUDGET, "sensitivity_p99": GRAD_BUDGET},
                        "parallelism": "replicas (independent shards)" if world > 1 else "single GPU",
