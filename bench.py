@@ -883,7 +883,7 @@ def run_case(args):
     --n orbits at --rtol, solved twice. 'fwd': persistent forward without a tape; 'fwdrev': forward
     recording its tape, then the persistent reverse sweep. --t1-myr shortens the orbits so that a
     case with several trajectories per lane keeps its tape to a few GB. 'prec': --n spin-precession
-    solves, FP64 Verner 7 persistent forward."""
+    solves, FP64 Verner 7 persistent forward. 'plain64': the FP64 plain-kernel baseline forward."""
     import torch
 
     from paper_2609_28458_gb300 import api
@@ -892,6 +892,17 @@ def run_case(args):
 
     gsbuild.build()
     dev = torch.device("cuda")
+    if args.case == "plain64":  # the FP64 one-thread-per-trajectory baseline, stored order, no tape
+        e = W.mw(n=args.n, seed=1000, t1=args.t1_myr)
+        y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
+        t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
+        for _ in range(2):
+            s = api.solve("mw", y0, pr, t0, t1, sv, RTOL_FWD_F64, RTOL_FWD_F64, precision="fp64", kernel="plain",
+                          order="natural")
+        torch.cuda.synchronize()
+        log("case plain64: n=%d failed=%d mean attempts %.1f" % (args.n, int((s["status"] != 0).sum()),
+                                                                float((s["n_accept"] + s["n_reject"]).double().mean())))
+        return
     if args.case == "prec":  # spin precession, FP64 Verner 7, persistent forward (the workload's kernel)
         p = W.precession(n=args.n, seed=2000)
         py0, pp = torch.as_tensor(p.y0, device=dev), torch.as_tensor(p.params, device=dev)
@@ -933,7 +944,7 @@ def main():
     ap.add_argument("--acc-sample", type=int, default=16384)
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--case", choices=["fwd", "fwdrev", "prec"], help="run a small profiling case instead")
+    ap.add_argument("--case", choices=["fwd", "fwdrev", "prec", "plain64"], help="run a small profiling case instead")
     ap.add_argument("--t1-myr", type=float, default=T1_MYR, help="orbit length of a --case run")
     ap.add_argument("--workload", default="mw",
                     choices=["mw", "isochrone", "precession", "precession_paper", "quintessence", "quintessence_flat",
