@@ -483,7 +483,9 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            # per step: the forward's cost estimate, histogram, scan and scatter of its longest-first
+            # work list and k_persist; the reverse's histogram, scan, scatter and k_reverse_persist
+            "gpu_launches": (5 + 4) * args.steps,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
