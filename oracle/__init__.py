@@ -16,7 +16,8 @@ import numpy as np
 
 from . import build as _build
 
-SYSTEMS = {"isochrone": 0, "mw": 1, "precession": 2, "quintessence": 3, "loghalo": 4}
+SYSTEMS = {"isochrone": 0, "mw": 1, "precession": 2, "quintessence": 3, "loghalo": 4,
+           "linear": 5}  # linear: the test equation y' = lambda y (tests of the controller only)
 METHODS = {"tsit5": 0, "dopri5": 1, "vern7": 2}
 ST_MAX_STEPS, ST_H_UNDERFLOW, ST_NONFINITE, ST_EMPTY_INTERVAL, ST_SAVEAT_OUTSIDE = 1, 2, 4, 8, 16
 

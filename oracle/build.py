@@ -20,14 +20,19 @@ def _stale() -> bool:
     return any(os.path.getmtime(os.path.join(HERE, f)) > t for f in SOURCES + HEADERS)
 
 
+def compile_lib(src_dir: str, out: str) -> str:
+    """Compile the oracle sources found in src_dir into the shared library `out`."""
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", out + ".tmp"] + [os.path.join(src_dir, s) for s in SOURCES]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
 def build(force: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-o", LIB + ".tmp"] + [os.path.join(HERE, s) for s in SOURCES]
-    subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    return compile_lib(HERE, LIB)
 
 
 if __name__ == "__main__":

@@ -10,7 +10,7 @@
 
 namespace orc {
 
-enum { S_ISOCHRONE = 0, S_MW = 1, S_PRECESSION = 2, S_QUINTESSENCE = 3, S_LOGHALO = 4 };
+enum { S_ISOCHRONE = 0, S_MW = 1, S_PRECESSION = 2, S_QUINTESSENCE = 3, S_LOGHALO = 4, S_LINEAR = 5 };
 
 inline void dims(int sys, int* d, int* p) {
   switch (sys) {
@@ -19,6 +19,7 @@ inline void dims(int sys, int* d, int* p) {
     case S_PRECESSION: *d = 9; *p = 3; return;
     case S_QUINTESSENCE: *d = 3; *p = 4; return;
     case S_LOGHALO: *d = 6; *p = 3; return;
+    case S_LINEAR: *d = 1; *p = 1; return;
     default: *d = 0; *p = 0;
   }
 }
@@ -174,12 +175,23 @@ void rhs_quintessence(const T& N, const T* y, const T* p, T* f) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Dahlquist's linear test equation y' = lambda y (d = 1, theta = lambda), the problem on which a
+// Runge-Kutta step reduces to multiplication by its stability polynomial (Hairer & Wanner II,
+// Sec. IV.2). Not one of the paper's systems: the tests use it to fix the error norm and the
+// step-size controller of Appendix A (Eqs. errnorm, controller) against a closed form.
+template <class T>
+void rhs_linear(const T* y, const T* p, T* f) {
+  f[0] = p[0] * y[0];
+}
+
+// ---------------------------------------------------------------------------------------------
 template <class T>
 void rhs(int sys, const T& t, const T* y, const T* p, T* f) {
   int d, np;
   dims(sys, &d, &np);
   if (sys == S_PRECESSION) rhs_precession(t, y, p, f);
   else if (sys == S_QUINTESSENCE) rhs_quintessence(t, y, p, f);
+  else if (sys == S_LINEAR) rhs_linear(y, p, f);
   else rhs_orbit(sys, y, p, np, f);
 }
 

@@ -69,6 +69,38 @@ def test_fp64_same_algorithm_parity(system, gen, method, kernel):
     assert np.array_equal(g["y"][empty], ref["y"][empty])
 
 
+PI_CASES = [
+    ("mw", lambda: W.mw(n=256, seed=41, t1=1500.0, rtol=1e-8), "tsit5"),
+    ("precession", lambda: W.precession(n=128, seed=42, paper_interval=True, rtol=1e-9), "vern7"),
+    ("isochrone", lambda: W.isochrone(n=256, seed=43), "dopri5"),
+]
+
+
+@pytest.mark.parametrize("system,gen,method", PI_CASES)
+@pytest.mark.parametrize("kernel", ["plain", "persistent"])
+def test_fp64_pi_controller_parity(system, gen, method, kernel):
+    """The PI form of Eq. controller with Gustafsson's gains (beta1, beta2) = (0.7/nu, 0.4/nu):
+    err_prev carried across accepted steps and reset to 1 by a rejection, in both kernels. Same
+    bar as the I-controller: members with the oracle's step counts agree to 1e-10 relative."""
+    e = gen()
+    nu = 7 if method == "vern7" else 5
+    kw = dict(beta1=0.7 / nu, beta2=0.4 / nu)
+    ref = oracle_solve(e, method=method, **kw)
+    g = gpu_solve(e, method=method, kernel=kernel, **kw)
+    assert np.array_equal(g["status"], ref["status"])
+    ok = (ref["status"] & O.ST_EMPTY_INTERVAL) == 0
+    same = (g["n_accept"] == ref["n_accept"]) & (g["n_reject"] == ref["n_reject"])
+    err = rel_err(g["y"], ref["y"])
+    assert same[ok].mean() >= 0.9, same[ok].mean()
+    assert err[same & ok].max() <= 1e-10, err[same & ok].max()
+    assert err[ok].max() <= 50 * e.rtol, err[ok].max()
+    # the gains reached the kernel (the step sequences differ from Eq. controller's) and the
+    # rejection branch, which resets err_prev, was taken
+    i_ctrl = oracle_solve(e, method=method)
+    assert np.any(i_ctrl["n_accept"][ok] != ref["n_accept"][ok])
+    assert ref["n_reject"][ok].sum() > 0
+
+
 def test_persistent_kernel_matches_plain():
     """Same per-trajectory algorithm in both kernels. FP64: the compiler may fuse multiply-adds
     differently in the two, so results agree to rounding and step counts almost always. FP32 modes:
