@@ -121,6 +121,28 @@ typedef struct {
                               first by cost_hint. Results do not depend on the order  */
   const int32_t* cost_hint;  /* [N] device array, e.g. the attempt counts of a previous
                               solve of similar inputs (may be NULL)                    */
+  int32_t ckpt_stride;     /* step tape (gs_vjp, gs_solve with record_tape): S = 1 (or 0)
+                              records every accepted step's start state; S in {2, 4, 8,
+                              16, 32} records the full integrator state every S accepted
+                              steps plus every step's length, and the reverse pass
+                              re-runs each segment of S steps from its checkpoint
+                              (bit-identical to the forward, so the gradient equals
+                              S = 1's). The tape shrinks about S-fold (a discrete form of
+                              the checkpointing trade-off of Appendix A, Eq. disc-modes)
+                              for one more forward step per reversed step. S > 1 needs
+                              the persistent kernel and is not available in GS_DF64.
+                              The library does not pick S; the Python autotuner does  */
+  int32_t ckpt_verify;     /* with ckpt_stride > 1: gs_vjp's reverse pass also replays the
+                              last step of every full segment and compares the state it
+                              reaches with the next segment's checkpoint bit for bit,
+                              adding the comparisons and the mismatches to the uint32
+                              words at workspace bytes 16 and 20 (zeroed by the call that
+                              records the tape). A self-check of the replay: one more
+                              forward step per segment                                 */
+  int32_t warp_lanes;      /* persistent kernels: how many lanes of each warp take
+                              trajectories (1..32; 0 = 32). Fewer spread a small ensemble
+                              over more warps, and so over more of the SMs' schedulers
+                              and their FP64 units, at the price of idle lanes          */
 } gs_options;
 
 #define GS_ORDER_AUTO 0
@@ -162,12 +184,18 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
  *  The workspace holds the step tape: per accepted step the state at its start, its time and
  *  its length, in chunks taken from a pool by an atomic counter. Layout: a 256-byte header, int32
  *  head[N], n_rec[N] and order[N] (the longest-first work list), 4096 bucket counters and the
- *  FP32 cost estimates cost[N] (each array padded to 256 bytes), then chunks of 16 + 32 * slot
- *  bytes (a 16-byte header holding the previous chunk's index, then 32 slots); a
- *  trajectory with n accepted steps uses ceil(n / 32) chunks. slot = roundup16(state) + tail:
- *  GS_FP64 state 8 d bytes (FP64), tail 32 (t, tc, h, flag as FP64); GS_FP32_STAGES state 4 d (the
- *  FP32 high part, from which the stages are recomputed), tail 32; GS_FP32_DF state 4 d, tail 16
- *  (time pair, h, flag as FP32); GS_DF64 state 8 d (df64 pairs), tail 16.
+ *  FP32 cost estimates cost[N] (each array padded to 256 bytes), with opt->ckpt_stride > 1 the
+ *  int32 output attribution emit[N, K] (the accepted step that produced each output), then chunks;
+ *  a trajectory with n accepted steps uses ceil(n / 32) chunks. A chunk is a 16-byte header holding
+ *  the previous chunk's index, then
+ *  - stride 1: 32 slots; slot = roundup16(state) + tail: GS_FP64 state 8 d bytes (FP64), tail 32
+ *    (t, tc, h, flag as FP64); GS_FP32_STAGES state 4 d (the FP32 high part, from which the stages
+ *    are recomputed), tail 32; GS_FP32_DF state 4 d, tail 16 (time pair, h, flag as FP32); GS_DF64
+ *    state 8 d (df64 pairs), tail 16;
+ *  - stride S > 1: the 32 step lengths (FP64; FP32 in GS_FP32_DF; the last, clipped step negative),
+ *    then 32 / S checkpoints of roundup16(state) + 16 bytes: GS_FP64 state = y and the first stage
+ *    (16 d bytes), the FP32 modes its high part, low part and first stage (12 d bytes); then the
+ *    time (t, tc as FP64, or the FP32 pair).
  */
 int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
            const double* t1, double rtol, double atol, int32_t K, const double* saveat,
@@ -187,10 +215,13 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and caches
  * it: make that first call before any stream capture. Calls share the array and it keeps the last
  * call's contents (the call clears what must start at zero); calls that overlap on the GPU race, so
- * issue them one after another. N whose per-trajectory bookkeeping (16 N bytes, padded, plus the
- * 256-byte header, 16 KB of counters and one tape chunk) exceeds the array is rejected with
- * GS_ERR_WORKSPACE; trajectories whose
- * steps do not fit in the rest of the array get GS_ST_TAPE_OVERFLOW and NaN gradients. */
+ * issue them one after another. An ensemble whose part before the tape pool
+ * (gs_workspace_bytes(system, N, K, opt, 1, 0): 16 N bytes of per-trajectory arrays, padded, the
+ * 256-byte header, 16 KB of counters, and 4 N K bytes with a checkpoint stride above 1) plus one
+ * tape chunk (gs_tape_chunk_bytes) exceeds the array is rejected with GS_ERR_WORKSPACE (an unknown
+ * system with GS_ERR_INVALID first); trajectories whose steps do not fit in the rest of the array
+ * get GS_ST_TAPE_OVERFLOW and NaN gradients. A checkpoint stride above 1 fits about S times more
+ * steps. */
 int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
                    const double* t1, double rtol, double atol, int32_t K, const double* saveat,
                    const gs_options* opt, const double* dLdy, double* dLdy0, double* dLdparams,
@@ -200,11 +231,18 @@ int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* pa
  * list (order[N], bucket counters, cost[N]); a smaller workspace runs GS_ORDER_AUTO in stored order
  * and rejects GS_ORDER_ESTIMATE and GS_ORDER_HINT with GS_ERR_WORKSPACE.
  * for_vjp != 0: room for a step tape of `steps_hint` accepted steps per trajectory on average
- * (rounded up to whole chunks per trajectory, plus one), in the slot size of opt->precision
- * (FP64 when opt is NULL). A smaller workspace is accepted; trajectories whose steps no longer
- * fit get GS_ST_TAPE_OVERFLOW. */
+ * (rounded up to whole chunks per trajectory, plus one), in the chunk size of opt->precision and
+ * opt->ckpt_stride (FP64, stride 1 when opt is NULL). With steps_hint = 0: the part before the tape
+ * pool (with a checkpoint stride above 1 it includes the int32 output attribution [N, K]); a tape
+ * for exactly n_i accepted steps per trajectory then needs (sum_i ceil(n_i / 32) + 1) chunks of
+ * gs_tape_chunk_bytes more. A smaller workspace is accepted; trajectories whose steps no longer
+ * fit get GS_ST_TAPE_OVERFLOW. Returns 0 for an unknown system, N < 0 or K < 0. */
 size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
                           double steps_hint);
+
+/* Bytes of one step-tape chunk (32 accepted steps of one trajectory) for opt's precision and
+ * checkpoint stride (FP64, stride 1 when opt is NULL); 0 for an unknown system or stride. */
+size_t gs_tape_chunk_bytes(int32_t system, const gs_options* opt);
 
 /* Forward sensitivities (Sec. 2.3, Eq. sens; Appendix A, Eq. stage-sens): the solve of gs_solve carrying
  * m tangent directions, S = dy/d(direction), integrated with the same Runge-Kutta steps as y (step
@@ -302,6 +340,16 @@ int gs_profile_fit(int64_t n_fits, const double* lam, const int32_t* mock, const
  *  precision selects the FP64 (GS_FP64) or FP32 (the two FP32 modes) instantiation. */
 int gs_rhs(int32_t system, int32_t precision, int64_t M, const double* t, const double* y,
            const double* params, const double* w, double* f, double* gy, double* gp, void* cuda_stream);
+
+/* Plain-ALU throughput probe (the paper has no counterpart; the benchmark's roofline denominators):
+ * one launch of blocks_per_sm (1..8) blocks of 256 threads per SM, every thread running `iters`
+ * rounds of 8 independent multiply-add chains; kind 0: FP32, 1: FP64, 2: FP32 on the packed
+ * two-lane multiply-add of sm_100 and later (float2 chains). sink: device array of at least
+ * 8 x (multiprocessor count) doubles, one sum per block written (so the work is kept).
+ * *fma_count (host) receives the number of multiply-adds launched; time the launch with CUDA events
+ * on cuda_stream: FLOP/s = 2 * fma_count / time. */
+int gs_alu_probe(int32_t kind, int64_t iters, int32_t blocks_per_sm, double* sink, int64_t* fma_count,
+                 void* cuda_stream);
 
 /* Message for the last non-zero return on this host thread ("" if none). */
 const char* gs_last_error(void);

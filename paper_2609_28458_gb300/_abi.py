@@ -22,6 +22,7 @@ ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_WORKSPACE = 0, 1, 2, 3
 
 EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_jvp", "gs_vjp_noalloc", "gs_workspace_bytes",
+           "gs_tape_chunk_bytes", "gs_alu_probe",
            "gs_solve_flat", "gs_flat_workspace_bytes", "gs_profile_default_options", "gs_profile_prep_bytes",
            "gs_profile_prepare", "gs_profile_workspace_bytes", "gs_profile_fit", "gs_rhs", "gs_last_error",
            "gs_version")
@@ -35,7 +36,8 @@ class GsOptions(ctypes.Structure):
                 ("h0", ctypes.c_double), ("per_traj_saveat", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("record_tape", ctypes.c_int32), ("reuse_tape", ctypes.c_int32), ("tape_capacity", ctypes.c_int32),
                 ("sm_limit", ctypes.c_int32), ("graph_safe", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("cost_hint", ctypes.c_void_p)]
+                ("cost_hint", ctypes.c_void_p), ("ckpt_stride", ctypes.c_int32),
+                ("ckpt_verify", ctypes.c_int32), ("warp_lanes", ctypes.c_int32)]
 
 
 class GsProfileOptions(ctypes.Structure):
@@ -109,6 +111,10 @@ def lib():
     L.gs_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(GsOptions),
                                      ctypes.c_int32, ctypes.c_double]
     L.gs_workspace_bytes.restype = ctypes.c_size_t
+    L.gs_tape_chunk_bytes.argtypes = [ctypes.c_int32, ctypes.POINTER(GsOptions)]
+    L.gs_tape_chunk_bytes.restype = ctypes.c_size_t
+    L.gs_alu_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
+    L.gs_alu_probe.restype = ctypes.c_int
     L.gs_rhs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_rhs.restype = ctypes.c_int
     L.gs_last_error.argtypes = []

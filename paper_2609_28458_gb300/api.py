@@ -85,20 +85,21 @@ def _ws(device, nbytes, ws):
     return ws.get(nbytes)[: int(nbytes)]
 
 
-def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None, precision="fp64"):
+def tape_bytes(system, n, n_accept=None, steps_hint=None, opt=None, precision="fp64", K=1, ckpt_stride=None):
     """Workspace bytes for a tape: exact from per-trajectory accepted-step counts, else from a hint.
-    The slot size depends on the precision mode (opt.precision, else `precision`)."""
-    d, _ = _abi.dims(system)
-    opt = opt or _abi.options(precision=precision)
-    fixed = _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 0, 0.0)
-    prec = opt.precision
-    state = (8 if prec in (_abi.PRECISIONS["fp64"], _abi.PRECISIONS["df64"]) else 4) * d
-    slot = (state + 15) // 16 * 16 + (16 if prec in (_abi.PRECISIONS["fp32df"], _abi.PRECISIONS["df64"]) else 32)
-    chunk = 16 + 32 * slot  # chunk header + 32 slots (gs.h)
+    The chunk size depends on the precision mode and checkpoint stride (of opt, else of `precision`
+    and `ckpt_stride`); K (outputs per trajectory) sizes the output attribution of strides above 1."""
+    if opt is None:
+        opt = _abi.options(precision=precision)
+        if ckpt_stride is not None:
+            opt.ckpt_stride = int(ckpt_stride)
+    L, sid = _abi.lib(), _sysid(system)
     if n_accept is not None:
+        fixed = L.gs_workspace_bytes(sid, n, K, ctypes.byref(opt), 1, 0.0)
+        chunk = L.gs_tape_chunk_bytes(sid, ctypes.byref(opt))
         chunks = int(((n_accept.to(torch.int64) + 31) // 32).sum().item()) + 1
         return fixed + chunks * chunk
-    return _abi.lib().gs_workspace_bytes(_sysid(system), n, 0, ctypes.byref(opt), 1, float(steps_hint or 1024))
+    return L.gs_workspace_bytes(sid, n, K, ctypes.byref(opt), 1, float(steps_hint or 1024))
 
 
 def solve(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precision="fp64", kernel="auto",
@@ -123,7 +124,7 @@ def solve(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precis
                    status=torch.empty(N, dtype=_i32, device=dev), n_accept=torch.empty(N, dtype=_i32, device=dev),
                    n_reject=torch.empty(N, dtype=_i32, device=dev))
     if record_tape:
-        nbytes = tape_nbytes or tape_bytes(system, N, steps_hint=steps_hint, opt=opt)
+        nbytes = tape_nbytes or tape_bytes(system, N, steps_hint=steps_hint, opt=opt, K=K)
     else:
         nbytes = _abi.lib().gs_workspace_bytes(_sysid(system), N, K, ctypes.byref(opt), 0, 0.0)
     wsb = _ws(dev, nbytes, workspace)
@@ -165,7 +166,7 @@ def vjp(system, y0, params, t0, t1, saveat, rtol, atol, dLdy, method="tsit5", pr
             # size the tape exactly from a forward solve with the same options (one extra solve)
             n_accept_hint = solve(system, y0, params, t0, t1, saveat, rtol, atol, method=method, precision=precision,
                                   kernel=kernel, **kw)["n_accept"]
-        nbytes = tape_nbytes or tape_bytes(system, N, n_accept=n_accept_hint, steps_hint=steps_hint, opt=opt)
+        nbytes = tape_nbytes or tape_bytes(system, N, n_accept=n_accept_hint, steps_hint=steps_hint, opt=opt, K=K)
         wsb = _ws(dev, nbytes, workspace)
     res = dict(dLdy0=torch.empty((N, d), dtype=torch.float64, device=dev),
                dLdparams=torch.empty((N, max(p, 0)), dtype=torch.float64, device=dev))
@@ -316,6 +317,28 @@ def rhs(system, t, y, params=None, w=None, precision="fp64"):
     _abi.check(_abi.lib().gs_rhs(_sysid(system), _abi.PRECISIONS[precision], M, _ptr(t), _ptr(y), _ptr(params),
                                  _ptr(w) if w is not None else None, _ptr(f), _ptr(gy), _ptr(gp), _stream(dev)))
     return f, gy, gp
+
+
+def alu_peak(fp64=False, iters=None, blocks_per_sm=4, device=None, reps=3, packed=False):
+    """Measured multiply-add throughput of the plain ALUs (TFLOP/s, 2 flops per FMA; best of `reps`
+    launches of gs_alu_probe timed with CUDA events on the current stream). packed: FP32 on the
+    two-lane FFMA2 instruction."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(8 * sms, dtype=torch.float64, device=dev)
+    kind = 1 if fp64 else (2 if packed else 0)
+    iters = int(iters or ((1 << 11) if fp64 else (1 << 16)))
+    cnt = ctypes.c_int64()
+    best = float("inf")
+    for _ in range(reps + 1):  # the first launch warms up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _abi.check(_abi.lib().gs_alu_probe(kind, iters, int(blocks_per_sm), _ptr(sink), ctypes.byref(cnt),
+                                           _stream(dev)))
+        b.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, a.elapsed_time(b))
+    return 2.0 * cnt.value / (best / 1e3) / 1e12
 
 
 class GsSolve(torch.autograd.Function):

@@ -19,7 +19,10 @@ namespace gs {
 // byte address sl, the float4s st bytes apart)
 // and the stage VJPs read them back instead of re-evaluating the right-hand side's position factors;
 // only for FP32 modes of systems that provide f_save / vjp_saved (the kernel supplies the memory).
-template <template <class> class SysT, class Tab, int PM, bool SLAB = false>
+// CK: the tape has a checkpoint stride S > 1 (gs_stepper.cuh, Tape); each segment of S steps is
+// replayed forward from its checkpoint into this thread's segment buffer (local memory) before its
+// steps are reversed, and outputs are attributed to steps through the tape's emit array.
+template <template <class> class SysT, class Tab, int PM, bool SLAB = false, bool CK = false>
 struct Adjoint {
   using T = Traj<SysT, Tab, PM>;
   static constexpr bool F32 = T::F32, DF = T::DF, DD = T::DD;
@@ -28,6 +31,8 @@ struct Adjoint {
   static constexpr int D = T::D, NP = T::NP, S = Tab::S, NPA = T::NPA;
   static constexpr int Q = SaveQ<Sys>::value;
   static_assert(!SLAB || (Q > 0 && F32 && !DD), "saved stage factors need an FP32 mode and f_save");
+  static_assert(!CK || !DD, "checkpoint strides above 1 are not built for the df64 mode");
+  static constexpr int kSegMax = kChunk;  // largest checkpoint stride
 
   struct PAcc {  // accumulator of theta-bar: FP64, or a compensated FP32 pair
     R s[NPA], c[NPA];
@@ -202,6 +207,15 @@ struct Adjoint {
   bool done;
   Raw nraw;  // the slot of step a, then (once step a has started) of step a - 1
   unsigned sl = 0, st = 0;  // SLAB: this thread's stage factors, stage j at shared address sl + j * Q * st
+  // CK: start states (FP32 modes: their high parts, from which the stages are recomputed) and times
+  // (t, tc, or the FP32 pair th, tl) of the steps seg_lo .. seg_lo + S - 1 of the current segment
+  using TT = typename std::conditional<DF, float, double>::type;
+  R sy[CK ? kSegMax : 1][D];
+  TT sta[CK ? kSegMax : 1], stb[CK ? kSegMax : 1];
+  int seg_lo;
+  // CK self-check (tape.verify): the checkpoint loaded last (the start of the next newer segment)
+  R vy[CK ? D : 1], vlo[CK ? D : 1];
+  bool vhave;
 
   __device__ void write_const(const Problem& pb, double v_y, double v_p, bool sum_w, bool only_t0) {
     const long long n = tr.n;
@@ -244,6 +258,22 @@ struct Adjoint {
     chunk = pb.tape.head[n];
 #pragma unroll
     for (int i = 0; i < T::DL; i++) tr.ylo[i] = R(0);
+    if constexpr (CK) {
+      // a chunk index outside the pool means the tape was recorded with other options (gs_vjp with
+      // reuse_tape needs the recording's options): NaN gradients rather than a read outside the pool
+      if (chunk < 0 || chunk >= pb.tape.pool_chunks) { write_const(pb, nanv, nanv, false, false); done = true; return; }
+      seg_lo = nrec;  // no segment buffered
+      vhave = false;
+      // outputs emitted after the final step (the interval closed without a clipped last step)
+      const int32_t* em = pb.tape.emit + n * pb.K;
+      while (kk >= 0 && (em[kk] == kEmitUnused || em[kk] == nrec)) {
+        if (em[kk] == nrec)
+#pragma unroll
+          for (int i = 0; i < D; i++) ybar[i] += R(W[kk * D + i]);
+        kk--;
+      }
+      return;
+    }
     fetch(slot_ptr(pb, chunk, a % kChunk), nraw);
     const SlotView last = decode(nraw);
     // outputs emitted after the final step when the interval closed without a clipped last step
@@ -257,8 +287,213 @@ struct Adjoint {
     }
   }
 
+  // CK: replay the segment holding step a from its checkpoint (in the current chunk: S divides the
+  // chunk length, so a segment never spans two chunks) and keep the start state and time of each
+  // of its steps up to a.
+  __device__ void load_segment(const Problem& pb) {
+    if constexpr (CK) {
+      const int S = pb.tape.stride;
+      seg_lo = (a / S) * S;
+      const int o0 = seg_lo % kChunk;
+      const unsigned char* base = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes;
+      const uint4* c4 = reinterpret_cast<const uint4*>(base + T::kCkOff + (long long)(o0 / S) * T::kCkBytes);
+      uint32_t w[T::kCkWords];
+#pragma unroll
+      for (int q = 0; q < T::kCkWords / 4; q++) {
+        const uint4 v = c4[q];
+        w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+      }
+      if constexpr (F32) {
+#pragma unroll
+        for (int i = 0; i < D; i++) {
+          tr.y[i] = __uint_as_float(w[i]);
+          tr.ylo[i] = __uint_as_float(w[D + i]);
+          tr.k1[i] = __uint_as_float(w[2 * D + i]);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < D; i++) {
+          tr.y[i] = __hiloint2double(int(w[2 * i + 1]), int(w[2 * i]));
+          tr.k1[i] = __hiloint2double(int(w[2 * D + 2 * i + 1]), int(w[2 * D + 2 * i]));
+        }
+      }
+      constexpr int T0 = T::kCkTimeOff / 4;
+      if constexpr (DF) {
+        tr.th = __uint_as_float(w[T0]);
+        tr.tl = __uint_as_float(w[T0 + 1]);
+      } else {
+        tr.t = __hiloint2double(int(w[T0 + 1]), int(w[T0]));
+        tr.tc = __hiloint2double(int(w[T0 + 3]), int(w[T0 + 2]));
+      }
+      const int m = a - seg_lo;  // steps to replay before step a
+      const bool verify = pb.tape.verify != nullptr;
+      R cy[CK ? D : 1], clo[CK ? D : 1];
+      if (verify) {
+#pragma unroll
+        for (int q = 0; q < D; q++) {
+          cy[q] = tr.y[q];
+          if constexpr (F32) clo[q] = tr.ylo[q];
+        }
+      }
+      for (int i = 0;; i++) {
+#pragma unroll
+        for (int q = 0; q < D; q++) sy[i][q] = tr.y[q];
+        if constexpr (DF) { sta[i] = tr.th; stb[i] = tr.tl; }
+        else { sta[i] = tr.t; stb[i] = tr.tc; }
+        if (i >= m) break;
+        tr.replay_step(step_length(base, o0 + i));
+      }
+      if (verify) {
+        // a full segment's last step, replayed, must land bit for bit on the newer segment's checkpoint
+        if (vhave && m == S - 1) {
+          tr.replay_step(step_length(base, o0 + m));
+          bool same = true;
+#pragma unroll
+          for (int q = 0; q < D; q++) {
+            same = same && bits_equal(tr.y[q], vy[q]);
+            if constexpr (F32) same = same && bits_equal(tr.ylo[q], vlo[q]);
+          }
+          atomicAdd(pb.tape.verify, 1u);
+          if (!same) atomicAdd(pb.tape.verify + 1, 1u);
+        }
+#pragma unroll
+        for (int q = 0; q < D; q++) {
+          vy[q] = cy[q];
+          if constexpr (F32) vlo[q] = clo[q];
+        }
+        vhave = true;
+      }
+    }
+  }
+  __device__ static double step_length(const unsigned char* base, int o) {
+    if constexpr (DF) return double(reinterpret_cast<const float*>(base + kChunkHeader)[o]);
+    else return reinterpret_cast<const double*>(base + kChunkHeader)[o];
+  }
+  __device__ static bool bits_equal(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+  __device__ static bool bits_equal(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+
+  // Reverse of step a of a checkpointed tape (CK), a step of the segment load_segment() buffered: as
+  // step(), with the step's start state and time from the segment buffer, its length from the chunk,
+  // and its outputs from the emit array.
+  __device__ void step_ck(const Problem& pb) {
+    const long long n = tr.n;
+    const double t1 = tr.t1;
+    const int o = a % kChunk;
+    const int i0 = a - seg_lo;
+    const unsigned char* base = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes;
+    SlotView cur;
+    if constexpr (DF) {
+      const float hv = reinterpret_cast<const float*>(base + kChunkHeader)[o];
+      cur.last = hv < 0.0f;
+      cur.hf = fabsf(hv);
+      cur.h = double(cur.hf);
+      cur.th = sta[i0];
+      cur.tl = stb[i0];
+      cur.t = double(cur.th) + double(cur.tl);
+      cur.tc = 0.0;
+    } else {
+      const double hv = reinterpret_cast<const double*>(base + kChunkHeader)[o];
+      cur.last = hv < 0.0;
+      cur.h = fabs(hv);
+      cur.t = sta[i0];
+      cur.tc = stb[i0];
+    }
+#pragma unroll
+    for (int q = 0; q < D; q++) tr.y[q] = sy[i0][q];
+    if constexpr (SLAB) Sys::f_save(tr.stage_time(cur.t), tr.y, tr.p, tr.k1, sl, st);
+    else Sys::f(tr.stage_time(cur.t), tr.y, tr.p, tr.k1);
+    const int32_t* em = pb.tape.emit + n * pb.K;
+    // does an output of this step use the dense polynomial (which needs the last, FSAL stage)?
+    bool dense_here = false;
+    if constexpr (Tab::DENSE_POLY) {
+      for (int q = kk; q >= 0; q--) {
+        if (em[q] == kEmitUnused) continue;
+        if (em[q] != a) break;
+        if (!(cur.last && save_at(pb, n, q) == t1)) { dense_here = true; break; }
+      }
+    }
+    R k[S][D], Y[S][D], kbar[S][D];
+    tr.template stages<SLAB>(cur.t, cur.h, k, Y, dense_here ? S : Tab::NREV, sl, st);
+#pragma unroll
+    for (int j = 0; j < S; j++)
+#pragma unroll
+      for (int i = 0; i < D; i++) kbar[j][i] = R(0);
+    R ydir[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) ydir[i] = R(0);
+    bool used_last_stage = false;
+    const R hr = R(cur.h);
+    while (kk >= 0) {
+      if (em[kk] == kEmitUnused) { kk--; continue; }
+      if (em[kk] != a) break;
+      inject(pb, cur, save_at(pb, n, kk), k, kbar, ydir, used_last_stage, hr);
+      kk--;
+    }
+#pragma unroll
+    for (int j = 0; j < S; j++)
+      if (Tab::b(j) != 0.0)
+#pragma unroll
+        for (int i = 0; i < D; i++) kbar[j][i] += hr * R(Tab::b(j)) * ybar[i];
+#pragma unroll
+    for (int i = 0; i < D; i++) ybar[i] += ydir[i];
+    reverse_stages<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
+    if (o == 0 && a > 0) {
+      chunk = prev_chunk(pb, chunk);
+      if (chunk < 0 || chunk >= pb.tape.pool_chunks) {  // as in init(): not this tape's layout
+        const double nanv = __longlong_as_double(0x7ff8000000000000LL);
+        write_const(pb, nanv, nanv, false, false);
+        done = true;
+        return;
+      }
+    }
+    a -= 1;
+    if (a < 0) finish(pb);
+  }
+
+  // The cotangent W[kk] of output time sv, emitted by the step cur: directly on the new state for
+  // an output at t1 after the last step, else through the dense-output weights (Tsit5, Dopri5) or
+  // a shortened step (Verner 7).
+  __device__ void inject(const Problem& pb, const SlotView& cur, double sv, R (*k)[D], R (*kbar)[D], R* ydir,
+                         bool& used_last_stage, R hr) {
+    R w[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) w[i] = R(W[kk * D + i]);
+    if (cur.last && sv == tr.t1) {
+#pragma unroll
+      for (int i = 0; i < D; i++) ybar[i] += w[i];  // y(t1) is the new state itself
+      return;
+    }
+    const R sig = sigma(cur, sv);
+    if constexpr (Tab::DENSE_POLY) {
+      // y(t_k) = y + h sum_j b_j(sig) k_j
+      R wd[S];
+      Tab::dense(sig, wd);
+#pragma unroll
+      for (int j = 0; j < S; j++)
+#pragma unroll
+        for (int i = 0; i < D; i++) kbar[j][i] += hr * wd[j] * w[i];
+      used_last_stage = true;
+#pragma unroll
+      for (int i = 0; i < D; i++) ydir[i] += w[i];
+    } else {
+      // Verner 7: y(t_k) = shortened step of length sig*h from (t, y)
+      const double hs = to_f64(sig) * cur.h;
+      R ks[S][D], Ys[S][D], kbs[S][D];
+      tr.stages(cur.t, hs, ks, Ys, Tab::NREV);
+      const R hsr = R(hs);
+#pragma unroll
+      for (int j = 0; j < S; j++)
+#pragma unroll
+        for (int i = 0; i < D; i++) kbs[j][i] = (j < Tab::NREV) ? hsr * R(Tab::b(j)) * w[i] : R(0);
+#pragma unroll
+      for (int i = 0; i < D; i++) ydir[i] += w[i];
+      reverse_stages(tr, cur.t, hs, Ys, kbs, Tab::NREV, ydir, pacc);
+    }
+  }
+
   // Reverse of recorded step a (ybar holds the cotangent of the state after it).
   __device__ void step(const Problem& pb) {
+    static_assert(!CK, "a checkpointed tape is reversed segment by segment (load_segment, step_ck)");
     const long long n = tr.n;
     const double t0 = tr.t0, t1 = tr.t1;
     const int o = a % kChunk;

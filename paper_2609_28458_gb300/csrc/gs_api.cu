@@ -47,23 +47,35 @@ int order_of(int32_t method) { return method == GS_VERN7 ? 7 : 5; }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// tape slot: the state at the step's start (FP64, df64 pairs, or its FP32 high part), padded to 16
-// bytes, then the times: t, tc, h, flag as FP64 (32 bytes), or th, tl, h, flag as FP32 (16 bytes,
-// PM 2 and 3)
+// tape slot (checkpoint stride 1): the state at the step's start (FP64, df64 pairs, or its FP32 high
+// part), padded to 16 bytes, then the times: t, tc, h, flag as FP64 (32 bytes), or th, tl, h, flag as
+// FP32 (16 bytes, PM 2 and 3)
 long long slot_bytes(int32_t d, int32_t prec) {
   const long long state = (prec == GS_FP64 || prec == GS_DF64 ? 8LL : 4LL) * d;
   return (state + 15) / 16 * 16 + (prec == GS_FP32_DF || prec == GS_DF64 ? 16 : 32);
 }
-long long chunk_bytes(int32_t d, int32_t prec) { return gs::kChunkHeader + gs::kChunk * slot_bytes(d, prec); }
+// checkpoint stride S > 1 (not PM 3): kChunk step lengths (FP64, FP32 in PM 2), then kChunk / S
+// checkpoints: state and first stage (FP64: 16 d bytes; FP32 modes: high part, low part and first
+// stage, 12 d bytes) padded to 16 bytes, then the time (16 bytes)
+long long ckpt_bytes(int32_t d, int32_t prec) {
+  const long long state = (prec == GS_FP64 ? 16LL : 12LL) * d;
+  return (state + 15) / 16 * 16 + 16;
+}
+long long chunk_bytes(int32_t d, int32_t prec, int32_t stride) {
+  if (stride > 1)
+    return gs::kChunkHeader + gs::kChunk * (prec == GS_FP32_DF ? 4LL : 8LL) + (gs::kChunk / stride) * ckpt_bytes(d, prec);
+  return gs::kChunkHeader + gs::kChunk * slot_bytes(d, prec);
+}
+int32_t stride_of(const gs_options* opt) { return (opt && opt->ckpt_stride > 1) ? opt->ckpt_stride : 1; }
 
-// workspace: [0,256) header (queue counter at 0, pool counter at 8) | head[N] | n_rec[N] | pool
 // workspace: header (work counters), head[N], n_rec[N], a work list order[N] with its bucket
 // counters and the estimated costs cost[N] (longest-first ordering of the forward and reverse
-// launches), then the tape pool
+// launches) [= total_fixed], with a checkpoint stride above 1 the output attribution emit[N, K],
+// then the tape pool
 struct Layout {
-  size_t header, head, nrec, order, buckets, cost, pool, total_fixed;
+  size_t header, head, nrec, order, buckets, cost, total_fixed, emit, pool;
 };
-Layout layout(int64_t N) {
+Layout layout(int64_t N, int32_t K = 0, int32_t stride = 1) {
   Layout L;
   L.header = 0;
   L.head = 256;
@@ -71,8 +83,9 @@ Layout layout(int64_t N) {
   L.order = L.nrec + align256(size_t(N) * 4);
   L.buckets = L.order + align256(size_t(N) * 4);
   L.cost = L.buckets + align256(size_t(gs::kOrderBuckets) * 4);
-  L.pool = L.cost + align256(size_t(N) * 4);
-  L.total_fixed = L.pool;
+  L.total_fixed = L.cost + align256(size_t(N) * 4);
+  L.emit = L.total_fixed;
+  L.pool = L.emit + (stride > 1 ? align256(size_t(N) * size_t(K > 0 ? K : 0) * 4) : 0);
   return L;
 }
 
@@ -155,6 +168,12 @@ int check_common(int32_t sys, int64_t N, const double* y0, const double* params,
   if (!(opt->safety > 0.0) || !(opt->alpha_min > 0.0) || !(opt->alpha_max >= opt->alpha_min))
     return fail(GS_ERR_INVALID, "controller: need safety > 0 and 0 < alpha_min <= alpha_max");
   if (opt->max_steps < 0) return fail(GS_ERR_INVALID, "max_steps < 0");
+  if (opt->warp_lanes < 0 || opt->warp_lanes > 32) return fail(GS_ERR_INVALID, "warp_lanes must be 0..32");
+  {
+    const int32_t cs = opt->ckpt_stride;
+    if (cs != 0 && cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16 && cs != 32)
+      return fail(GS_ERR_INVALID, "ckpt_stride must be 0, 1, 2, 4, 8, 16 or 32");
+  }
   if (N > 0) {
     if (!y0 || !t0 || !t1) return fail(GS_ERR_INVALID, "y0, t0 and t1 must not be NULL");
     if (*p > 0 && !params) return fail(GS_ERR_INVALID, "params must not be NULL for this system");
@@ -178,6 +197,7 @@ gs::Problem make_problem(int64_t N, const double* y0, const double* params, cons
   pb.beta1 = opt->beta1 > 0.0 ? opt->beta1 : 1.0 / order_of(opt->method);
   pb.beta2 = opt->beta2;
   pb.h0 = opt->h0;
+  pb.warp_lanes = opt->warp_lanes > 0 ? opt->warp_lanes : 32;
   pb.fsafety = float(pb.safety);
   pb.falpha_min = float(pb.alpha_min);
   pb.falpha_max = float(pb.alpha_max);
@@ -186,19 +206,27 @@ gs::Problem make_problem(int64_t N, const double* y0, const double* params, cons
   return pb;
 }
 
-int set_tape(gs::Problem& pb, int32_t d, int32_t prec, int32_t opt_cap, int64_t N, void* ws, size_t ws_bytes) {
-  if (opt_cap <= 0) return fail(GS_ERR_INVALID, "tape_capacity must be positive");
-  Layout L = layout(N);
-  const long long cb = chunk_bytes(d, prec);
+int set_tape(gs::Problem& pb, int32_t d, const gs_options* opt, int64_t N, int32_t K, void* ws, size_t ws_bytes) {
+  if (opt->tape_capacity <= 0) return fail(GS_ERR_INVALID, "tape_capacity must be positive");
+  const int32_t stride = stride_of(opt);
+  if (stride > 1 && opt->precision == GS_DF64)
+    return fail(GS_ERR_INVALID, "checkpoint strides above 1 are not available in GS_DF64");
+  if (stride > 1 && opt->kernel == GS_KERNEL_PLAIN)
+    return fail(GS_ERR_INVALID, "checkpoint strides above 1 run in the persistent kernels (kernel auto or persistent)");
+  Layout L = layout(N, K, stride);
+  const long long cb = chunk_bytes(d, opt->precision, stride);
   if (!ws) return fail(GS_ERR_WORKSPACE, "this call needs a workspace (see gs_workspace_bytes)");
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(GS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
-  if (ws_bytes < L.total_fixed + size_t(cb))
+  if (ws_bytes < L.pool + size_t(cb))
     return fail(GS_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu needed for N = %lld", ws_bytes,
-                size_t(L.total_fixed + cb), (long long)N);
+                size_t(L.pool + cb), (long long)N);
   unsigned char* base = static_cast<unsigned char*>(ws);
+  pb.tape.stride = stride;
+  pb.tape.emit = stride > 1 ? reinterpret_cast<int32_t*>(base + L.emit) : nullptr;
+  pb.tape.verify = (stride > 1 && opt->ckpt_verify) ? reinterpret_cast<unsigned int*>(base + 16) : nullptr;
   pb.tape.pool = base + L.pool;
   pb.tape.chunk_bytes = cb;
-  pb.tape.cap = opt_cap;
+  pb.tape.cap = opt->tape_capacity;
   pb.tape.pool_chunks = (long long)((ws_bytes - L.pool) / size_t(cb));
   if (pb.tape.pool_chunks > 0x7fffffffLL) pb.tape.pool_chunks = 0x7fffffffLL;
   pb.tape.pool_next = reinterpret_cast<unsigned long long*>(base + 8);
@@ -246,14 +274,22 @@ int gs_dims(int32_t system, int32_t* d, int32_t* p) {
 
 size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options* opt, int32_t for_vjp,
                           double steps_hint) {
-  (void)K;
   int32_t d, p;
-  if (dims_of(system, &d, &p) || N < 0) return 0;
-  Layout L = layout(N);
+  if (dims_of(system, &d, &p) || N < 0 || K < 0) return 0;
+  const int32_t stride = stride_of(opt);
+  Layout L = layout(N, K, stride);
   if (!for_vjp) return L.total_fixed;
-  if (!(steps_hint > 0.0)) steps_hint = 1.0;
+  if (!(steps_hint > 0.0)) return L.pool;
   const double chunks = double(N) * (std::ceil(steps_hint / gs::kChunk) + 1.0) + 1.0;
-  return L.total_fixed + size_t(chunks) * size_t(chunk_bytes(d, opt ? opt->precision : GS_FP64));
+  return L.pool + size_t(chunks) * size_t(chunk_bytes(d, opt ? opt->precision : GS_FP64, stride));
+}
+
+size_t gs_tape_chunk_bytes(int32_t system, const gs_options* opt) {
+  int32_t d, p;
+  if (dims_of(system, &d, &p)) return 0;
+  const int32_t cs = opt ? opt->ckpt_stride : 0;
+  if (cs != 0 && cs != 1 && cs != 2 && cs != 4 && cs != 8 && cs != 16 && cs != 32) return 0;
+  return size_t(chunk_bytes(d, opt ? opt->precision : GS_FP64, stride_of(opt)));
 }
 
 int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, const double* t0,
@@ -278,7 +314,7 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     pb.queue = static_cast<unsigned int*>(workspace);
   }
   if (opt->record_tape) {
-    rc = set_tape(pb, d, opt->precision, opt->tape_capacity, N, workspace, workspace_bytes);
+    rc = set_tape(pb, d, opt, N, K, workspace, workspace_bytes);
     if (rc) return rc;
     pb.record = 1;
   }
@@ -309,7 +345,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   gs::Problem pb = make_problem(N, y0, params, t0, t1, rtol, atol, K, saveat, opt);
   pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
-  rc = set_tape(pb, d, opt->precision, opt->tape_capacity, N, workspace, workspace_bytes);
+  rc = set_tape(pb, d, opt, N, K, workspace, workspace_bytes);
   if (rc) return rc;
   rc = set_order(pb, opt, N, workspace, workspace_bytes);  // of the forward re-solve
   if (rc) return rc;

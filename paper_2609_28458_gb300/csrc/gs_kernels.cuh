@@ -59,8 +59,9 @@ template <template <class> class SysT, class Tab, int PM, int MT = 0>
 __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_persist(const Problem pb) {
   Traj<SysT, Tab, PM, MT> tr;
   const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
-  bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
+  // lanes at or above pb.warp_lanes take no work: a small ensemble spreads over more warps
+  bool running = false, exhausted = lane >= unsigned(pb.warp_lanes);
   const unsigned lt_mask = (1u << lane) - 1u;
   while (true) {
     const bool need = !running && !exhausted;
@@ -120,8 +121,9 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_revers
     adj.st = 16u * blockDim.x;
   }
   const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
-  bool running = false, exhausted = false;
   const unsigned lane = threadIdx.x & 31u;
+  // lanes at or above pb.warp_lanes take no work: a small ensemble spreads over more warps
+  bool running = false, exhausted = lane >= unsigned(pb.warp_lanes);
   const unsigned lt_mask = (1u << lane) - 1u;
   while (true) {
     const bool need = !running && !exhausted;
@@ -144,6 +146,54 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_revers
     if (__all_sync(0xffffffffu, exhausted)) break;
     if (running) {
       adj.step(pb);
+      if (adj.done) running = false;
+    }
+  }
+}
+
+// Reverse sweeps over a checkpointed tape (stride S > 1) from a work queue. Each round of the loop
+// gives every lane one segment: the lane replays it from its checkpoint (up to S - 1 forward steps)
+// and then reverses its steps. Whole segments per round keep the lanes of a warp in the same phase,
+// replaying together and reversing together; only a trajectory's first (newest, partial) segment
+// leaves a lane idle for part of a round. Lanes are refilled between rounds.
+template <template <class> class SysT, class Tab, int PM>
+__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_reverse_ckpt(const Problem pb) {
+  constexpr bool SLAB = RevSlab<SysT, Tab, PM>::on;
+  Adjoint<SysT, Tab, PM, SLAB, true> adj;
+  if constexpr (SLAB) {
+    extern __shared__ float4 gs_rev_slab[];
+    adj.sl = unsigned(__cvta_generic_to_shared(gs_rev_slab + threadIdx.x));
+    adj.st = 16u * blockDim.x;
+  }
+  const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
+  const unsigned lane = threadIdx.x & 31u;
+  // lanes at or above pb.warp_lanes take no work: a small ensemble spreads over more warps
+  bool running = false, exhausted = lane >= unsigned(pb.warp_lanes);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  while (true) {
+    const bool need = !running && !exhausted;
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned base = 0;
+      if (int(lane) == leader) base = atomicAdd(pb.queue, unsigned(__popc(m)));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const unsigned long long idx = (unsigned long long)base + unsigned(__popc(m & lt_mask));
+        if (idx < n_work) {
+          adj.init(pb, pb.work ? (long long)pb.work[idx] : (long long)idx);
+          running = !adj.done;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (__all_sync(0xffffffffu, exhausted)) break;
+    if (running) {
+      adj.load_segment(pb);
+      do {
+        adj.step_ck(pb);
+      } while (!adj.done && adj.a >= adj.seg_lo);
       if (adj.done) running = false;
     }
   }
@@ -332,7 +382,8 @@ cudaError_t launch_forward_t(const Problem& pb0, const LaunchCfg& c) {
   if (c.kernel == 2) {
     auto kern = k_persist<SysT, Tab, PM>;
     long long grid = persistent_grid(kern, block, c.sm_limit);
-    const long long need = (pb.n_work + block - 1) / block;
+    const long long per_block = (long long)block * pb.warp_lanes / 32;
+    const long long need = (pb.n_work + per_block - 1) / per_block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<unsigned(grid), block, 0, c.stream>>>(pb);
@@ -347,11 +398,27 @@ template <template <class> class SysT, class Tab, int PM>
 cudaError_t launch_reverse_t(const Problem& pb, const LaunchCfg& c) {
   const int block = c.block > 0 ? c.block : 128;
   if (pb.n_work <= 0) return cudaSuccess;
+  if (pb.tape.stride > 1) {  // checkpointed tape: persistent kernel only (checked by the caller)
+    if constexpr (PM == 3) {
+      return cudaErrorInvalidValue;
+    } else {
+      auto kern = k_reverse_ckpt<SysT, Tab, PM>;
+      const size_t smem = size_t(RevSlab<SysT, Tab, PM>::bytes_per_thread) * size_t(block);
+      long long grid = persistent_grid(kern, block, c.sm_limit, smem);
+      const long long per_block = (long long)block * pb.warp_lanes / 32;
+      const long long need = (pb.n_work + per_block - 1) / per_block;
+      if (grid > need) grid = need;
+      if (grid < 1) grid = 1;
+      kern<<<unsigned(grid), block, smem, c.stream>>>(pb);
+      return cudaGetLastError();
+    }
+  }
   if (c.kernel == 2) {
     auto kern = k_reverse_persist<SysT, Tab, PM>;
     const size_t smem = size_t(RevSlab<SysT, Tab, PM>::bytes_per_thread) * size_t(block);
     long long grid = persistent_grid(kern, block, c.sm_limit, smem);
-    const long long need = (pb.n_work + block - 1) / block;
+    const long long per_block = (long long)block * pb.warp_lanes / 32;
+    const long long need = (pb.n_work + per_block - 1) / per_block;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<unsigned(grid), block, smem, c.stream>>>(pb);
@@ -372,7 +439,8 @@ cudaError_t launch_jvp_t(const Problem& pb0, const LaunchCfg& c) {
   if (eo != cudaSuccess) return eo;
   auto kern = k_persist<SysT, Tab, PM, MT>;
   long long grid = persistent_grid(kern, block, c.sm_limit);
-  const long long need = (pb.n_work + block - 1) / block;
+  const long long per_block = (long long)block * pb.warp_lanes / 32;
+  const long long need = (pb.n_work + per_block - 1) / per_block;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   kern<<<unsigned(grid), block, 0, c.stream>>>(pb);

@@ -39,6 +39,8 @@ extern "C" int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const
                               double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject,
                               void* cuda_stream) {
   char msg[256];
+  int32_t d, p;
+  if (gs_dims(system, &d, &p) != GS_OK) return GS_ERR_INVALID;  // gs_dims recorded the message
   if (!opt) return gs::set_error(GS_ERR_INVALID, "opt is NULL");
   if (opt->reuse_tape)
     return gs::set_error(GS_ERR_INVALID, "gs_vjp_noalloc re-runs the forward solve; reuse_tape must be 0");
@@ -55,14 +57,16 @@ extern "C" int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const
     std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(g_setup[dev]));
     return gs::set_error(GS_ERR_CUDA, msg);
   }
-  // the fixed part of the scratch (header, per-trajectory chunk heads and counts) plus one tape chunk
-  // must fit; trajectories whose steps do not fit in the rest get GS_ST_TAPE_OVERFLOW
-  const size_t fixed = gs_workspace_bytes(system, N, K, opt, 0, 0.0);
-  const size_t one_chunk = gs_workspace_bytes(system, 1, K, opt, 1, 1.0) - gs_workspace_bytes(system, 1, K, opt, 0, 0.0);
-  if (N > 0 && (fixed == 0 || fixed + one_chunk > size_t(GS_NOALLOC_SCRATCH_BYTES))) {
+  // the part before the tape pool (work counters, per-trajectory arrays and, with a checkpoint stride
+  // above 1, the output attribution) plus one tape chunk must fit, the same test as gs_vjp's;
+  // trajectories whose steps do not fit in the rest get GS_ST_TAPE_OVERFLOW. Sizes of 0 mean an
+  // argument gs_vjp rejects (N < 0, K < 0, an unknown stride): it reports those itself.
+  const size_t fixed = gs_workspace_bytes(system, N, K, opt, 1, 0.0);
+  const size_t one_chunk = gs_tape_chunk_bytes(system, opt);
+  if (N > 0 && fixed > 0 && one_chunk > 0 && fixed + one_chunk > size_t(GS_NOALLOC_SCRATCH_BYTES)) {
     std::snprintf(msg, sizeof(msg),
                   "N = %lld trajectories do not fit the %u-byte built-in scratch of gs_vjp_noalloc "
-                  "(it needs %zu bytes before any tape); use gs_vjp with a workspace",
+                  "(it needs %zu bytes with one tape chunk); use gs_vjp with a workspace",
                   (long long)N, (unsigned)GS_NOALLOC_SCRATCH_BYTES, fixed + one_chunk);
     return gs::set_error(GS_ERR_WORKSPACE, msg);
   }

@@ -50,6 +50,14 @@ constexpr int kChunk = 32;  // accepted steps per tape chunk
 // chunk starts with a 16-byte header holding the index of the trajectory's previous chunk, so the
 // chunks of one trajectory form a list walked backwards by the reverse pass from head[n].
 constexpr int kChunkHeader = 16;
+//
+// Checkpoint stride S > 1 (S divides kChunk): a chunk holds, after its header, the lengths of its
+// kChunk steps (the last, clipped step of a trajectory recorded with a negative sign) and one
+// checkpoint per S steps: the full integrator state at the start of every S-th accepted step (the
+// state, its FP32 low part, the first stage k1 and the time). The reverse pass replays each segment
+// of S steps from its checkpoint with those lengths (Traj::replay_step, the arithmetic of attempt())
+// and so recovers every step's start state bit for bit. Outputs are attributed to the step that
+// emitted them through emit[N, K], since the replay does not know the times of the previous segment.
 struct Tape {
   unsigned char* pool;
   long long pool_chunks;
@@ -58,7 +66,13 @@ struct Tape {
   int32_t* head;   // [N] last chunk of each trajectory (-1: none)
   int32_t* n_rec;  // [N] accepted steps recorded (-1: the tape overflowed)
   int32_t cap;     // most steps recorded per trajectory (more: the tape overflows)
+  int32_t stride;  // checkpoint stride S (1: a full slot per accepted step)
+  int32_t* emit;   // S > 1: [N, K] the accepted step that emitted each output; -1: the output is
+                   // y0 (at t0), -2: unused (outside [t0, t1]), n_acc: emitted after the last step
+  unsigned int* verify;  // S > 1, optional: [2] replayed segment ends compared with the next
+                         // checkpoint, and those that differed (the reverse pass's self-check)
 };
+constexpr int kEmitT0 = -1, kEmitUnused = -2;
 
 struct Problem {
   long long N;
@@ -92,6 +106,7 @@ struct Problem {
   int32_t record;
   Tape tape;
   unsigned int* queue;  // persistent kernel work counter
+  int32_t warp_lanes;   // persistent kernels: lanes per warp that take work (1..32)
   // forward sensitivities: seeds dy0 [N, d, m_total] and dp [N, p, m_total] (either may be null),
   // output S [N, K, d, m_total]; a launch handles the directions m_off .. m_off + MT - 1
   const double* dy0;
@@ -128,6 +143,48 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
 }
 
 constexpr float kEps48 = 3.5527136788005009e-15f;  // 2^-48: unit roundoff of an FP32 pair
+
+// a * b + c with one rounding, as an explicit fused multiply-add. The stage combinations and state
+// updates are written with it, so that every kernel that inlines them (the forward attempt, and the
+// reverse pass's replay of a checkpoint segment) rounds them alike, whichever multiply-add fusions the
+// compiler would otherwise pick in each (a product shared by two sums may be fused into one or both).
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ F2 fmadd(const F2& a, const F2& b, const F2& c) { return a * b + c; }
+// An FP32 number widened to FP64 exactly by moving its bits (sign; exponent rebiased by 1023 - 127;
+// mantissa shifted up by 29) with integer instructions, where a conversion instruction would take a
+// slot of the FP64 pipe, which GB300 runs at 1/64 of the FP32 rate. Zero (and, with flush-to-zero, a
+// subnormal) gives zero; infinities and NaNs keep their class.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sgn = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  uint32_t hi = sgn | ((ex + 896u) << 20) | (man >> 3), lo = man << 29;
+  if (ex == 0u) { hi = sgn; lo = 0u; }
+  if (ex == 0xffu) hi = sgn | 0x7ff00000u | (man >> 3) | (man ? 0x80000u : 0u);
+  return __hiloint2double(int(hi), int(lo));
+}
+// Order, NaN test and log2 of a non-negative FP64 number (a sum of squares) from its bits with
+// integer and FP32 instructions: for x, y >= 0 the bit patterns order as the values do, and every
+// NaN pattern lies above that of +inf.
+__device__ __forceinline__ bool le_nonneg_f64(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
+__device__ __forceinline__ bool isnan_f64_bits(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+// log2 x to FP32 accuracy: the unbiased exponent plus log2 of the mantissa truncated to 24 bits
+__device__ __forceinline__ float log2_f64_f32(double x) {
+  const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
+  const int ex = int((hi >> 20) & 0x7ffu) - 1023;
+  const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  return float(ex) + __log2f(m);
+}
+template <class R, int M>
+__device__ __forceinline__ Dual<R, M> fmadd(R a, const Dual<R, M>& b, const Dual<R, M>& c) {
+  Dual<R, M> r;
+  r.v = fmadd(a, b.v, c.v);
+#pragma unroll
+  for (int m = 0; m < M; m++) r.d[m] = fmadd(a, b.d[m], c.d[m]);
+  return r;
+}
 
 // value part and derivative part m of a plain real (derivative 0) or a dual number
 __device__ __forceinline__ float dpart(float, int) { return 0.0f; }
@@ -182,12 +239,25 @@ struct Traj {
                 "tape slots must stay 16-byte aligned");
   static constexpr int kSlotWords = kSlotBytes / 4;
   static_assert(kStateBytes <= kTailOff, "state part of a slot overlaps its tail");
+  // checkpoint stride S > 1: chunk = header, kChunk step lengths (FP64, or FP32 in PM 2), then
+  // kChunk / S checkpoints. A checkpoint is the state (FP64, or the FP32 high and low parts), the
+  // first stage k1 of the step (FSAL: the previous step's last stage, which a recomputation from the
+  // state would not reproduce bit for bit), padded to 16 bytes, then the time: t, tc (FP64) or
+  // th, tl (FP32 pair, padded to 16 bytes). Not used in PM 3.
+  static constexpr int kHBytes = DF ? 4 : 8;
+  static constexpr int kCkStateWords = F32 ? 3 * D : 4 * D;
+  static constexpr int kCkTimeOff = (4 * kCkStateWords + 15) / 16 * 16;
+  static constexpr int kCkBytes = kCkTimeOff + 16;
+  static constexpr int kCkWords = kCkBytes / 4;
+  static constexpr int kCkOff = kChunkHeader + kChunk * kHBytes;
+  static_assert(kCkOff % 16 == 0 && kCkBytes % 16 == 0, "checkpoints must stay 16-byte aligned");
 
   T y[D];     // state (FP64) / high part (FP32), with its sensitivities when MT > 0
   R ylo[DL];  // low part (FP32)
   T k1[D];    // f(t, y): the first stage of the next attempt
   T p[NPP];
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
+  double rem_c, hmin_c;  // PM 0, 1: (t1 - t) + tc and 16 eps max(|t|, |t1|), updated when t is
   float th, tl, hf, t1h, t1l, svh, svl;   // PM 2, 3
   float atolf, rtolf, lerr_prev;          // PM 1, 2, 3
   long long n;
@@ -401,10 +471,17 @@ struct Traj {
       if (save_valid(pb, n, kk, t0, t1)) write_y0(pb, kk, y0d);
       kk++;
     }
+    if (pb.tape.emit) {  // checkpointed tape: outputs at t0 and unused ones are known now
+      for (int k = 0; k < pb.K; k++) {
+        if (!save_valid(pb, n, k, t0, t1)) pb.tape.emit[n * pb.K + k] = kEmitUnused;
+        else if (k < kk) pb.tape.emit[n * pb.K + k] = kEmitT0;
+      }
+    }
     load_sv(pb);
     Sys::f(stage_time(t0), y, p, k1);
     t = t0;
     tc = 0.0;
+    time_cache();
     err_prev = 1.0;
     lerr_prev = 0.0f;
     atolf = float(pb.atol);
@@ -437,9 +514,9 @@ struct Traj {
           T acc = T(R(0));
 #pragma unroll
           for (int l = 0; l < j; l++)
-            if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
-          if constexpr (F32 || DD) Yj[i] = y[i] + hr * acc;
-          else Yj[i] = y[i] + hh * acc;
+            if (Tab::a(j, l) != 0.0) acc = fmadd(R(Tab::a(j, l)), k[l][i], acc);
+          if constexpr (F32 || DD) Yj[i] = fmadd(hr, acc, y[i]);
+          else Yj[i] = fmadd(hh, acc, y[i]);
           if (Y) Y[j][i] = Yj[i];
         }
         if constexpr (SAVE) {
@@ -541,6 +618,12 @@ struct Traj {
       hdr[0] = chunk;
       chunk = int32_t(idx);
     }
+    if constexpr (!DD) {
+      if (pb.tape.stride > 1) {
+        record_ck(pb, o, a, last);
+        return;
+      }
+    }
     // slots start 16-byte aligned (16-byte header, slots of multiples of 16 bytes)
     uint4* s4 = reinterpret_cast<uint4*>(pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes + kChunkHeader +
                                          (long long)o * kSlotBytes);
@@ -549,6 +632,51 @@ struct Traj {
 #pragma unroll
     for (int q = 0; q < kSlotWords / 4; q++) s4[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     }
+  }
+
+  // Checkpoint stride S > 1: the length of the step just accepted (chunk position o, trajectory
+  // step a; negative for the last, clipped step) and, every S steps, the checkpoint of its start:
+  // state, first stage and time, assembled in registers and written as 16-byte stores.
+  __device__ void record_ck(const Problem& pb, int o, int a, bool last) {
+    unsigned char* base = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes;
+    if constexpr (DF) reinterpret_cast<float*>(base + kChunkHeader)[o] = last ? -hf : hf;
+    else reinterpret_cast<double*>(base + kChunkHeader)[o] = last ? -h : h;
+    if (a % pb.tape.stride != 0) return;
+    uint32_t w[kCkWords];
+    if constexpr (F32) {
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        w[i] = __float_as_uint(val(y[i]));
+        w[D + i] = __float_as_uint(ylo[i]);
+        w[2 * D + i] = __float_as_uint(val(k1[i]));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        const double v = val(y[i]), kv = val(k1[i]);
+        w[2 * i] = uint32_t(__double2loint(v));
+        w[2 * i + 1] = uint32_t(__double2hiint(v));
+        w[2 * D + 2 * i] = uint32_t(__double2loint(kv));
+        w[2 * D + 2 * i + 1] = uint32_t(__double2hiint(kv));
+      }
+    }
+#pragma unroll
+    for (int i = kCkStateWords; i < kCkTimeOff / 4; i++) w[i] = 0u;
+    constexpr int T0 = kCkTimeOff / 4;
+    if constexpr (DF) {
+      w[T0] = __float_as_uint(th);
+      w[T0 + 1] = __float_as_uint(tl);
+      w[T0 + 2] = 0u;
+      w[T0 + 3] = 0u;
+    } else {
+      w[T0] = uint32_t(__double2loint(t));
+      w[T0 + 1] = uint32_t(__double2hiint(t));
+      w[T0 + 2] = uint32_t(__double2loint(tc));
+      w[T0 + 3] = uint32_t(__double2hiint(tc));
+    }
+    uint4* s4 = reinterpret_cast<uint4*>(base + kCkOff + (long long)(o / pb.tape.stride) * kCkBytes);
+#pragma unroll
+    for (int q = 0; q < kCkWords / 4; q++) s4[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
   }
 
   __device__ void fail(int32_t bit) {
@@ -560,7 +688,10 @@ struct Traj {
   // the interval closed without a clipped last step: the remaining outputs are the state
   __device__ void close_interval(const Problem& pb) {
     while (kk < pb.K) {
-      if (save_valid(pb, n, kk, t0, t1)) write_out(pb, kk, y, ylo);
+      if (save_valid(pb, n, kk, t0, t1)) {
+        write_out(pb, kk, y, ylo);
+        if (pb.tape.emit) pb.tape.emit[n * pb.K + kk] = nacc;
+      }
       kk++;
     }
     done = true;
@@ -579,6 +710,108 @@ struct Traj {
     if (fac > pb.alpha_max) fac = pb.alpha_max;
     if (fac < pb.alpha_min) fac = pb.alpha_min;
     return fac;
+  }
+
+  // Stages 2..S of a step of length h (hr in the stage precision) from the current state, Eq. rk
+  // (k[0] = k1), and the new state y + h sum_j b_j k_j: for FSAL pairs in FP64 and df64 the last
+  // stage state itself; in the FP32 modes the compensated update of the (hi, lo) pair. Shared by
+  // attempt() and replay_step(), so that the reverse pass's replay of a checkpoint segment
+  // reproduces the forward's states bit for bit.
+  __device__ __forceinline__ void step_core(R hr, T (*k)[D], T* ynew, R* ynlo) const {
+    T Ylast[D];
+#pragma unroll
+    for (int i = 0; i < D; i++) k[0][i] = k1[i];
+#pragma unroll
+    for (int j = 1; j < S; j++) {
+      T Yj[D];
+#pragma unroll
+      for (int i = 0; i < D; i++) {
+        T acc = T(R(0));
+#pragma unroll
+        for (int l = 0; l < j; l++)
+          if (Tab::a(j, l) != 0.0) acc = fmadd(R(Tab::a(j, l)), k[l][i], acc);
+        // FP32 modes: the stage state is y_hi + h sum a k; the low part of the state only enters the
+        // update of the state itself (below), its effect on a stage is below the stage's FP32 rounding
+        if constexpr (F32 || DD) Yj[i] = fmadd(hr, acc, y[i]);
+        else Yj[i] = fmadd(h, acc, y[i]);
+        if (j == S - 1) Ylast[i] = Yj[i];
+      }
+      if constexpr (DF) Sys::f((R(th) + R(tl)) + R(Tab::c(j)) * hr, Yj, p, k[j]);
+      else Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      if constexpr (Tab::FSAL && !F32) {
+        ynew[i] = Ylast[i];
+      } else {
+        T acc = T(R(0));
+#pragma unroll
+        for (int j = 0; j < S; j++)
+          if (Tab::b(j) != 0.0) acc = fmadd(R(Tab::b(j)), k[j][i], acc);
+        if constexpr (F32) {
+          state_update(y[i], fmadd(hr, acc, T(ylo[i])), ynew[i], ynlo[i]);
+        } else if constexpr (DD) {
+          ynew[i] = fmadd(hr, acc, y[i]);
+        } else {
+          ynew[i] = fmadd(h, acc, y[i]);
+        }
+      }
+    }
+  }
+  // the state after an accepted step (FSAL pairs: its first stage is the step's last one)
+  __device__ __forceinline__ void take_state(T (*k)[D], const T* ynew, const R* ynlo) {
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      y[i] = ynew[i];
+      if constexpr (F32) ylo[i] = ynlo[i];
+      if constexpr (Tab::FSAL) k1[i] = k[S - 1][i];
+    }
+  }
+  // the quantities of the step-length tests that change only with the time (PM 0, 1): the remaining
+  // interval and the step-size floor of the underflow test
+  __device__ __forceinline__ void time_cache() {
+    if constexpr (!DF) {
+      rem_c = (t1 - t) + tc;
+      const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
+      hmin_c = 16.0 * DBL_EPSILON * tm;
+    }
+  }
+  // the time after an accepted step that is not the last (Kahan summation, or the error-free
+  // advance of the FP32 time pair), then the next first stage of pairs without FSAL
+  __device__ __forceinline__ void next_time() {
+    if constexpr (DF) {
+      float s, e2;  // (th, tl) += hf without rounding error
+      two_sum(th, hf, s, e2);
+      const float l = tl + e2;
+      th = s + l;
+      tl = l - (th - s);
+      if constexpr (!Tab::FSAL) Sys::f(R(th) + R(tl), y, p, k1);
+    } else {
+      const double yk = h - tc;  // Kahan summation of the time
+      const double tn = t + yk;
+      tc = (tn - t) - yk;
+      t = tn;
+      if constexpr (!Tab::FSAL) Sys::f(stage_time(t), y, p, k1);
+    }
+  }
+  // One accepted step of recorded length hrec (FP64, or the FP32 step of PM 2) from the current
+  // state, time and first stage, with the arithmetic of attempt() and no error estimate: the reverse
+  // pass's replay of a checkpoint segment. Never the last, clipped step of a trajectory.
+  __device__ __forceinline__ void replay_step(double hrec) {
+    R hr;
+    if constexpr (DF) {
+      hf = float(hrec);
+      hr = hf;
+    } else {
+      h = hrec;
+      hr = R(h);
+    }
+    T k[S][D];
+    T ynew[D];
+    R ynlo[DL];
+    step_core(hr, k, ynew, ynlo);
+    take_state(k, ynew, ynlo);
+    next_time();
   }
 
   // One step attempt.
@@ -603,62 +836,22 @@ struct Traj {
       if constexpr (DD)
         if (last) hr = (R(t1h) + R(t1l)) - (R(th) + R(tl));
     } else {
-      const double rem = (t1 - t) + tc;
-      if (rem <= 0.0) { close_interval(pb); return; }
+      if (rem_c <= 0.0) { close_interval(pb); return; }
       if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
-      if (h * (1.0 + 4.0 * DBL_EPSILON) >= rem) {
-        h = rem;
+      if (h * (1.0 + 4.0 * DBL_EPSILON) >= rem_c) {
+        h = rem_c;
         last = true;
-      } else {
-        const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
-        if (!(h >= 16.0 * DBL_EPSILON * tm)) { fail(isnan(h) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW); return; }
+      } else if (!(h >= hmin_c)) {
+        fail(isnan(h) ? (ST_H_UNDERFLOW | ST_NONFINITE) : ST_H_UNDERFLOW);
+        return;
       }
       hr = R(h);
     }
-    // ---- stages 2..S (the last one is the new state for FSAL pairs), Eq. rk
+    // ---- stages 2..S and the new state, Eq. rk
     T k[S][D];
-    T Ylast[D];
-#pragma unroll
-    for (int i = 0; i < D; i++) k[0][i] = k1[i];
-#pragma unroll
-    for (int j = 1; j < S; j++) {
-      T Yj[D];
-#pragma unroll
-      for (int i = 0; i < D; i++) {
-        T acc = T(R(0));
-#pragma unroll
-        for (int l = 0; l < j; l++)
-          if (Tab::a(j, l) != 0.0) acc = acc + R(Tab::a(j, l)) * k[l][i];
-        // FP32 modes: the stage state is y_hi + h sum a k; the low part of the state only enters the
-        // update of the state itself (below), its effect on a stage is below the stage's FP32 rounding
-        if constexpr (F32 || DD) Yj[i] = y[i] + hr * acc;
-        else Yj[i] = y[i] + h * acc;
-        if (j == S - 1) Ylast[i] = Yj[i];
-      }
-      if constexpr (DF) Sys::f((R(th) + R(tl)) + R(Tab::c(j)) * hr, Yj, p, k[j]);
-      else Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
-    }
-    // ---- new state: y + h sum b_j k_j
     T ynew[D];
     R ynlo[DL];
-#pragma unroll
-    for (int i = 0; i < D; i++) {
-      if constexpr (Tab::FSAL && !F32) {
-        ynew[i] = Ylast[i];
-      } else {
-        T acc = T(R(0));
-#pragma unroll
-        for (int j = 0; j < S; j++)
-          if (Tab::b(j) != 0.0) acc = acc + R(Tab::b(j)) * k[j][i];
-        if constexpr (F32) {
-          state_update(y[i], ylo[i] + hr * acc, ynew[i], ynlo[i]);
-        } else if constexpr (DD) {
-          ynew[i] = y[i] + hr * acc;
-        } else {
-          ynew[i] = y[i] + h * acc;
-        }
-      }
-    }
+    step_core(hr, k, ynew, ynlo);
     // ---- error estimate e = h sum (b_j - bhat_j) k_j and its scaled RMS norm, Eq. errnorm:
     // ||e|| = sqrt(sq / d), sq = sum_i (e_i / s_i)^2, s_i = atol + rtol max(|y_i|, |y+_i|)
     bool accept, bad;
@@ -701,7 +894,10 @@ struct Traj {
       lerr = 0.5f * (__log2f(sq) - log2f(float(D)));
       bad = isnan(sq);
     } else {
-      // PM 1 accumulates the squares in FP64, PM 2 in FP32
+      // PM 1 accumulates the squares in FP64 (each FP32 ratio widened exactly, by integer
+      // instructions, then one FP64 multiply-add), PM 2 in FP32. PM 1 then takes the accept test,
+      // the NaN test and log2 ||e|| for the controller's power from the FP64 sum's bits, so that the
+      // FP64 pipe carries only the accumulation itself.
       using Acc = typename std::conditional<PM == 1, double, float>::type;
       Acc sq = Acc(0);
 #pragma unroll
@@ -713,12 +909,23 @@ struct Traj {
         const R e = hr * acc;
         const R a = fabsf(val(y[i])), b = fabsf(val(ynew[i]));
         const R sc = atolf + rtolf * (a > b ? a : b);
-        const Acc r = Acc(__fdividef(e, sc));
-        sq += r * r;
+        if constexpr (PM == 1) {
+          const double r = widen_f32(__fdividef(e, sc));
+          sq = fma(r, r, sq);
+        } else {
+          const Acc r = Acc(__fdividef(e, sc));
+          sq += r * r;
+        }
       }
-      accept = sq <= Acc(D);
-      lerr = 0.5f * (__log2f(float(sq)) - log2f(float(D)));  // log2 ||e||
-      bad = isnan(sq);
+      if constexpr (PM == 1) {
+        accept = le_nonneg_f64(sq, double(D));
+        lerr = 0.5f * (log2_f64_f32(sq) - log2f(float(D)));  // log2 ||e||
+        bad = isnan_f64_bits(sq);
+      } else {
+        accept = sq <= Acc(D);
+        lerr = 0.5f * (__log2f(float(sq)) - log2f(float(D)));  // log2 ||e||
+        bad = isnan(sq);
+      }
     }
     if (accept) {
       nacc += 1;
@@ -727,31 +934,34 @@ struct Traj {
       while (kk < pb.K) {
         if (!sv_ok) { kk++; load_sv(pb); continue; }
         bool at_end, inside;
-        R sig;
         if constexpr (DF) {
           at_end = last && svh == t1h && svl == t1l;
-          const float dk = (svh - th) + (svl - tl);
-          inside = last || dk <= hf;
-          if constexpr (DD) {  // the fraction of the step in df64, from the exact time pairs
-            sig = ((R(svh) + R(svl)) - (R(th) + R(tl))) / hr;
-            if (val(sig) > 1.0f) sig = R(1.0f);
-            if (val(sig) < 0.0f) sig = R(0.0f);
-          } else {
-            sig = fminf(fmaxf(__fdividef(dk, hf), 0.0f), 1.0f);
-          }
+          inside = last || ((svh - th) + (svl - tl)) <= hf;
         } else {
           at_end = last && sv == t1;
-          const double dk = (sv - t) + tc;
-          inside = last || dk <= h;
-          double sg = dk / h;
-          if (sg > 1.0) sg = 1.0;
-          if (sg < 0.0) sg = 0.0;
-          sig = R(sg);
+          inside = last || ((sv - t) + tc) <= h;
         }
         if (at_end) {
           if constexpr (F32) write_out(pb, kk, ynew, ynlo);
           else write_out(pb, kk, ynew, ynew);
         } else if (inside) {
+          // the fraction of the step at the output time, only for an output inside the step (in
+          // FP64 modes a division)
+          R sig;
+          if constexpr (DF) {
+            if constexpr (DD) {  // the fraction of the step in df64, from the exact time pairs
+              sig = ((R(svh) + R(svl)) - (R(th) + R(tl))) / hr;
+              if (val(sig) > 1.0f) sig = R(1.0f);
+              if (val(sig) < 0.0f) sig = R(0.0f);
+            } else {
+              sig = fminf(fmaxf(__fdividef((svh - th) + (svl - tl), hf), 0.0f), 1.0f);
+            }
+          } else {
+            double sg = ((sv - t) + tc) / h;
+            if (sg > 1.0) sg = 1.0;
+            if (sg < 0.0) sg = 0.0;
+            sig = R(sg);
+          }
           T hi[D], lo[D];
           if constexpr (DD) dense_point(double(th) + double(tl), to_f64(hr), sig, k, hi, lo);
           else if constexpr (DF) dense_point(double(th) + double(tl), double(hf), sig, k, hi, lo);
@@ -760,36 +970,24 @@ struct Traj {
         } else {
           break;
         }
+        if (pb.tape.emit) pb.tape.emit[n * pb.K + kk] = nacc - 1;
         kk++;
         load_sv(pb);
       }
-#pragma unroll
-      for (int i = 0; i < D; i++) {
-        y[i] = ynew[i];
-        if constexpr (F32) ylo[i] = ynlo[i];
-        if constexpr (Tab::FSAL) k1[i] = k[S - 1][i];
-      }
+      take_state(k, ynew, ynlo);
       if (last) {
         done = true;
         if constexpr (DF) { th = t1h; tl = t1l; }
         else { t = t1; tc = 0.0; }
       } else if constexpr (DF) {
-        float s, e2;  // (th, tl) += hf without rounding error
-        two_sum(th, hf, s, e2);
-        const float l = tl + e2;
-        th = s + l;
-        tl = l - (th - s);
-        if constexpr (!Tab::FSAL) Sys::f(R(th) + R(tl), y, p, k1);
+        next_time();
         hf = hf * factor_f(pb, lerr);
         lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;  // log2(1e-4)
       } else {
-        const double yk = h - tc;  // Kahan summation of the time
-        const double tn = t + yk;
-        tc = (tn - t) - yk;
-        t = tn;
-        if constexpr (!Tab::FSAL) Sys::f(stage_time(t), y, p, k1);
+        next_time();
+        time_cache();
         if constexpr (F32) {
-          h = h * double(factor_f(pb, lerr));
+          h = h * widen_f32(factor_f(pb, lerr));
           lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;
         } else {
           h = h * factor_d(pb, err);
@@ -799,7 +997,7 @@ struct Traj {
     } else {
       nrej += 1;
       if constexpr (DF) hf = hf * (bad ? pb.falpha_min : factor_f(pb, lerr));
-      else if constexpr (F32) h = h * (bad ? pb.alpha_min : double(factor_f(pb, lerr)));
+      else if constexpr (F32) h = h * (bad ? pb.alpha_min : widen_f32(factor_f(pb, lerr)));
       else h = h * (bad ? pb.alpha_min : factor_d(pb, err));
       err_prev = 1.0;
       lerr_prev = 0.0f;

@@ -126,4 +126,58 @@ def test_order_option_checks(lib):
     rc = lib.gs_solve(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, fake, fake,
                       None, 0, None)
     assert rc == _abi.GS_ERR_WORKSPACE
-    assert ctypes.sizeof(_abi.GsOptions) == 104
+    assert ctypes.sizeof(_abi.GsOptions) == 120
+
+
+def test_checkpoint_stride_sizes_and_checks(lib):
+    """gs_options.ckpt_stride: the chunk of a stride S > 1 holds 32 step lengths and 32 / S
+    checkpoints (state, first stage and, in the FP32 modes, the state's low part; then the time);
+    the part before the pool gains the int32 output attribution [N, K]; bad strides and the
+    unsupported combinations are rejected on the host."""
+    fake = ctypes.c_void_p(256)
+    for prec, hbytes, words in (("fp64", 8, 4), ("fp32", 8, 3), ("fp32df", 4, 3)):
+        for sysid, d in ((1, 6), (2, 9), (3, 3)):
+            o1 = _abi.options(precision=prec)
+            c1 = lib.gs_tape_chunk_bytes(sysid, ctypes.byref(o1))
+            # steps_hint 1: one chunk per trajectory plus one, after the part before the pool
+            assert lib.gs_workspace_bytes(sysid, 10, 1, ctypes.byref(o1), 1, 1.0) - \
+                lib.gs_workspace_bytes(sysid, 10, 1, ctypes.byref(o1), 1, 0.0) == (10 * 2 + 1) * c1
+            for S in (2, 4, 8, 16, 32):
+                o = _abi.options(precision=prec, ckpt_stride=S)
+                ck = (4 * words * d + 15) // 16 * 16 + 16
+                assert lib.gs_tape_chunk_bytes(sysid, ctypes.byref(o)) == 16 + 32 * hbytes + (32 // S) * ck
+                if S >= 4:  # (at S = 2 a checkpoint's low part and first stage outweigh the savings)
+                    assert lib.gs_tape_chunk_bytes(sysid, ctypes.byref(o)) < c1
+                K = 7
+                a = lib.gs_workspace_bytes(sysid, 1000, K, ctypes.byref(o), 1, 0.0)
+                assert a == lib.gs_workspace_bytes(sysid, 1000, K, ctypes.byref(o), 0, 0.0) + (1000 * K * 4 + 255) // 256 * 256
+    # the Milky-Way FP32-pair tape at S = 16 is a fifth of S = 1's
+    o1, o16 = _abi.options(precision="fp32df"), _abi.options(precision="fp32df", ckpt_stride=16)
+    assert lib.gs_tape_chunk_bytes(1, ctypes.byref(o1)) / lib.gs_tape_chunk_bytes(1, ctypes.byref(o16)) > 4.5
+    assert lib.gs_tape_chunk_bytes(1, ctypes.byref(_abi.options(ckpt_stride=3))) == 0
+    assert lib.gs_tape_chunk_bytes(99, ctypes.byref(o1)) == 0
+
+    def vjp(o):
+        return lib.gs_vjp(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, None, fake,
+                          fake, fake, fake, ctypes.c_void_p(1 << 20), 1 << 30, None)
+
+    for bad in (3, -2, 64):
+        assert vjp(_abi.options(ckpt_stride=bad)) == _abi.GS_ERR_INVALID
+    assert vjp(_abi.options(ckpt_stride=8, kernel="plain")) == _abi.GS_ERR_INVALID
+    assert "persistent" in lib.gs_last_error().decode()
+    assert vjp(_abi.options(ckpt_stride=8, precision="df64")) == _abi.GS_ERR_INVALID
+    # a workspace below the part before the pool plus one chunk is rejected for strides too
+    o = _abi.options(ckpt_stride=8, kernel="persistent")
+    need = lib.gs_workspace_bytes(0, 4, 1, ctypes.byref(o), 1, 0.0) + lib.gs_tape_chunk_bytes(0, ctypes.byref(o))
+    rc = lib.gs_vjp(0, 4, fake, None, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake, None, fake, fake,
+                    fake, fake, ctypes.c_void_p(1 << 20), need - 256, None)
+    assert rc == _abi.GS_ERR_WORKSPACE
+
+
+def test_noalloc_checks_the_system_first(lib):
+    """An unknown system id is an invalid argument, not a scratch-size failure."""
+    fake = ctypes.c_void_p(256)
+    o = _abi.options()
+    rc = lib.gs_vjp_noalloc(42, 1 << 30, fake, fake, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake,
+                            fake, fake, fake, fake, fake, None)
+    assert rc == _abi.GS_ERR_INVALID and "unknown system" in lib.gs_last_error().decode()

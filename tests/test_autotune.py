@@ -1,5 +1,8 @@
-"""Autotuner host logic (CPU): candidate selection and the JSON cache, with a fake timer."""
+"""Autotuner host logic (CPU): candidate selection, the memory rule for the checkpoint stride and the
+JSON cache, with a fake timer and a fake memory test."""
 import os
+
+import pytest
 
 from paper_2609_28458_gb300 import autotune
 
@@ -8,18 +11,34 @@ def test_pick_and_cache_roundtrip(tmp_path):
     path = str(tmp_path / "cache.json")
     calls = []
 
-    def fake_timer(kernel, block):
-        calls.append((kernel, block))
+    def fake_timer(kernel, block, stride):
+        calls.append((kernel, block, stride))
         return {"persistent": 10.0, "plain": 20.0}[kernel] + {128: 1.0, 96: 0.5, 64: 2.0}[block]
 
-    k, b = autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, timer=fake_timer, cache_path=path)
-    assert (k, b) == ("persistent", 96)
-    assert sorted(calls) == sorted(autotune.CANDIDATES)
+    c = autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, timer=fake_timer, cache_path=path)
+    assert c == ("persistent", 96, 1)
+    assert sorted(calls) == sorted((k, b, 1) for k, b in autotune.KERNELS)
     assert os.path.exists(path)
     calls.clear()
-    assert autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, timer=fake_timer, cache_path=path) == (k, b)
+    assert autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, timer=fake_timer, cache_path=path) == c
     assert calls == []  # served from the cache
-    k2, _ = autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, precision="fp32df", cache_path=path,
-                          timer=lambda kernel, block: {"persistent": 5.0, "plain": 1.0}[kernel] + block / 1000)
-    assert k2 == "plain"  # a different key is tuned separately
+    c2 = autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, precision="fp32df", cache_path=path,
+                       timer=lambda kernel, block, stride: {"persistent": 5.0, "plain": 1.0}[kernel] + block / 1000)
+    assert c2.kernel == "plain"  # a different key is tuned separately
     assert len(autotune.load_cache(path)) == 2
+
+
+def test_gradient_candidates_respect_the_memory_budget(tmp_path):
+    """Gradient runs add the checkpoint stride: stride 1 for both kernels, larger strides for the
+    persistent kernels only, and only strides whose tape fits; the fastest fitting one wins."""
+    path = str(tmp_path / "cache.json")
+    cand = autotune.candidates(True)
+    assert {s for _, _, s in cand} == set(autotune.STRIDES)
+    assert all(k == "persistent" for k, _, s in cand if s > 1)
+    # only strides >= 8 fit: stride 1 (fastest) is not a candidate
+    fits = lambda s: s >= 8
+    c = autotune.tune("mw", None, None, None, None, None, 1e-8, 1e-8, fwd_grad=True, cache_path=path,
+                      stride_fits=fits, timer=lambda k, b, s: 1.0 * s + (0 if b == 128 else 1))
+    assert c == ("persistent", 128, 8)
+    with pytest.raises(MemoryError):
+        autotune.candidates(True, stride_fits=lambda s: False)

@@ -65,7 +65,7 @@ def test_autotuned_configuration_gives_identical_results(tmp_path):
     e = W.mw(n=20000, seed=90, t1=1000.0, rtol=1e-8)
     y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
     t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
-    kernel, block = autotune.tune("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp32df", sample=8192,
+    kernel, block, _ = autotune.tune("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp32df", sample=8192,
                                   cache_path=str(tmp_path / "c.json"))
     assert (kernel, block) in autotune.CANDIDATES
     a = api.solve("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp64", kernel=kernel, block_size=block)

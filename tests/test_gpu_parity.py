@@ -80,8 +80,16 @@ PI_CASES = [
 @pytest.mark.parametrize("kernel", ["plain", "persistent"])
 def test_fp64_pi_controller_parity(system, gen, method, kernel):
     """The PI form of Eq. controller with Gustafsson's gains (beta1, beta2) = (0.7/nu, 0.4/nu):
-    err_prev carried across accepted steps and reset to 1 by a rejection, in both kernels. Same
-    bar as the I-controller: members with the oracle's step counts agree to 1e-10 relative."""
+    err_prev carried across accepted steps and reset to 1 by a rejection, in both kernels.
+
+    Tolerance. The PI controller carries rounding noise of the error estimate (which cancels its
+    leading terms: ~eps h|f| / (rtol |y|), 1e-8 relative at rtol 1e-8) from step to step instead of
+    resetting it each step, so its step sequence depends on the order of rounding far more than
+    Eq. controller's: the oracle's own source compiled with multiply-add contraction against without
+    it, on the Milky-Way case here, differs by up to 8.7e-9 relative on members with equal step
+    counts (P90 1.2e-10) under the PI gains, and by 1.3e-12 under Eq. controller. The GPU fuses
+    multiply-adds and the oracle does not, so the bar is that spread: members with the oracle's step
+    counts within 5 rtol and their median within 1e-10; every member within 50 rtol."""
     e = gen()
     nu = 7 if method == "vern7" else 5
     kw = dict(beta1=0.7 / nu, beta2=0.4 / nu)
@@ -92,7 +100,8 @@ def test_fp64_pi_controller_parity(system, gen, method, kernel):
     same = (g["n_accept"] == ref["n_accept"]) & (g["n_reject"] == ref["n_reject"])
     err = rel_err(g["y"], ref["y"])
     assert same[ok].mean() >= 0.9, same[ok].mean()
-    assert err[same & ok].max() <= 1e-10, err[same & ok].max()
+    assert err[same & ok].max() <= 5 * e.rtol, err[same & ok].max()
+    assert np.median(err[same & ok]) <= 1e-10, np.median(err[same & ok])
     assert err[ok].max() <= 50 * e.rtol, err[ok].max()
     # the gains reached the kernel (the step sequences differ from Eq. controller's) and the
     # rejection branch, which resets err_prev, was taken
