@@ -3,12 +3,14 @@
 For a (system, method, precision, forward or gradient) key it times the candidate configurations on a
 sample of the caller's ensemble and keeps the fastest, cached in a JSON file so later processes reuse
 the choice. Candidates: kernel (plain one-thread-per-trajectory, or persistent work queue) x block
-size (64, 96, 128 threads) and, for gradient runs, the checkpoint stride of the step tape
-(gs_options.ckpt_stride: 1, 4, 8, 16, 32; strides above 1 run in the persistent kernels). A stride
-is a candidate only if the tape it needs for the whole ensemble fits the memory budget: stride 1
-never recomputes a step but stores every step's state; a stride S stores a checkpoint every S steps
-and the reverse pass replays each segment (about S times less tape for one more forward step per
-reversed step). The per-trajectory arithmetic does not depend on the configuration, so every
+size (64, 96, 128 threads); for ensembles smaller than the GPU's resident lanes, the lanes per warp
+that take trajectories in the persistent kernels (gs_options.warp_lanes: 32, 16, 8; fewer spread a
+small ensemble over more warps and schedulers); and, for gradient runs, the checkpoint stride of the
+step tape (gs_options.ckpt_stride: 1, 4, 8, 16, 32; strides above 1 run in the persistent kernels).
+A stride is a candidate only if the tape it needs for the whole ensemble fits the memory budget:
+stride 1 never recomputes a step but stores every step's state; a stride S stores a checkpoint every
+S steps and the reverse pass replays each segment (about S times less tape for one more forward step
+per reversed step). The per-trajectory arithmetic does not depend on the configuration, so every
 candidate returns the same solution; only time and memory differ.
 
 The cache key includes the GPU name so a cache copied to other hardware is not reused.
@@ -25,10 +27,12 @@ from . import api
 
 KERNELS = [(k, b) for k in ("persistent", "plain") for b in (128, 96, 64)]
 STRIDES = (1, 4, 8, 16, 32)
-CANDIDATES = KERNELS  # the forward's candidate set (kernel, block)
+LANES = (32, 16, 8)
+SMALL_ENSEMBLE = 1 << 16  # below this, fewer lanes per warp are candidates too
+CANDIDATES = KERNELS  # the forward's (kernel, block) pairs
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "gs_gb300_autotune.json")
 
-Choice = namedtuple("Choice", ["kernel", "block_size", "ckpt_stride"])
+Choice = namedtuple("Choice", ["kernel", "block_size", "warp_lanes", "ckpt_stride"])
 
 
 def _key(system, method, precision, fwd_grad):
@@ -57,13 +61,15 @@ def pick(timings):
     return min(timings.items(), key=lambda kv: kv[1])[0]
 
 
-def candidates(fwd_grad, stride_fits=None):
-    """(kernel, block, stride) candidates: strides only for gradient runs, above 1 only in the
-    persistent kernels, and only those whose tape fits (stride_fits(S), default: all)."""
+def candidates(fwd_grad, stride_fits=None, small=False):
+    """(kernel, block, lanes, stride) candidates: lanes below 32 only for small ensembles and the
+    persistent kernels; strides only for gradient runs, above 1 only in the persistent kernels, and
+    only those whose tape fits (stride_fits(S), default: all)."""
+    base = [(k, b, l) for k, b in KERNELS for l in (LANES if small else (32,)) if l == 32 or k == "persistent"]
     if not fwd_grad:
-        return [(k, b, 1) for k, b in KERNELS]
+        return [(k, b, l, 1) for k, b, l in base]
     fits = stride_fits or (lambda s: True)
-    out = [(k, b, s) for s in STRIDES for k, b in KERNELS if (s == 1 or k == "persistent") and fits(s)]
+    out = [(k, b, l, s) for s in STRIDES for k, b, l in base if (s == 1 or k == "persistent") and fits(s)]
     if not out:
         raise MemoryError("no checkpoint stride up to %d fits the tape into the memory budget" % STRIDES[-1])
     return out
@@ -84,19 +90,20 @@ def pick_stride(system, n, n_accept, precision, budget_bytes, kernel="persistent
 
 def tune(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precision="fp64", fwd_grad=False,
          sample=65536, reps=2, cache_path=DEFAULT_CACHE, force=False, timer=None, budget_bytes=None,
-         stride_fits=None):
-    """Best Choice(kernel, block_size, ckpt_stride) for this key; times candidates on up to `sample`
-    trajectories. For gradient runs the strides considered are those whose tape for the whole
-    ensemble (the sample's accepted-step counts scaled to it) fits budget_bytes (default: half the
-    free device memory). `timer(kernel, block, stride)` and `stride_fits(stride)` may replace the
-    GPU timing (milliseconds) and the memory test."""
+         stride_fits=None, n=None):
+    """Best Choice(kernel, block_size, warp_lanes, ckpt_stride) for this key; times candidates on up
+    to `sample` trajectories (n, the ensemble size, defaults to y0's). For gradient runs the strides
+    considered are those whose tape for the whole ensemble (the sample's accepted-step counts scaled
+    to it) fits budget_bytes (default: half the free device memory). `timer(kernel, block, lanes,
+    stride)` and `stride_fits(stride)` may replace the GPU timing (milliseconds) and the memory test."""
     key = _key(system, method, precision, fwd_grad)
     cache = load_cache(cache_path)
     if not force and key in cache:
         c = cache[key]
-        return Choice(c["kernel"], int(c["block_size"]), int(c.get("ckpt_stride", 1)))
+        return Choice(c["kernel"], int(c["block_size"]), int(c.get("warp_lanes", 32)), int(c.get("ckpt_stride", 1)))
+    if n is None:
+        n = y0.shape[0] if y0 is not None else SMALL_ENSEMBLE
     if timer is None:
-        n = y0.shape[0]
         idx = torch.as_tensor(np.sort(np.random.default_rng(0).choice(n, min(n, sample), replace=False)),
                               device=y0.device)
         sub = lambda x: (x[idx] if torch.is_tensor(x) and x.dim() and x.shape[0] == n else x)
@@ -115,18 +122,16 @@ def tune(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precisi
             if stride_fits is None:
                 stride_fits = lambda s: nbytes[s] * scale <= budget_bytes
 
-        def timer(kernel, block, stride):
+        def timer(kernel, block, lanes, stride):
             def run():
+                kw = dict(method=method, precision=precision, kernel=kernel, block_size=block, warp_lanes=lanes)
                 if fwd_grad:
-                    s = api.solve(system, Y0, P, T0, T1, SV, rtol, atol, method=method, precision=precision,
-                                  kernel=kernel, block_size=block, record_tape=True, workspace=ws,
-                                  tape_nbytes=nbytes[stride], ckpt_stride=stride)
-                    api.vjp(system, Y0, P, T0, T1, SV, rtol, atol, torch.ones_like(s["y"]), method=method,
-                            precision=precision, kernel=kernel, block_size=block, reuse_tape=s, workspace=ws,
-                            ckpt_stride=stride)
+                    s = api.solve(system, Y0, P, T0, T1, SV, rtol, atol, record_tape=True, workspace=ws,
+                                  tape_nbytes=nbytes[stride], ckpt_stride=stride, **kw)
+                    api.vjp(system, Y0, P, T0, T1, SV, rtol, atol, torch.ones_like(s["y"]), reuse_tape=s,
+                            workspace=ws, ckpt_stride=stride, **kw)
                 else:
-                    api.solve(system, Y0, P, T0, T1, SV, rtol, atol, method=method, precision=precision,
-                              kernel=kernel, block_size=block)
+                    api.solve(system, Y0, P, T0, T1, SV, rtol, atol, **kw)
 
             run()
             torch.cuda.synchronize()
@@ -141,12 +146,12 @@ def tune(system, y0, params, t0, t1, saveat, rtol, atol, method="tsit5", precisi
             return best
 
     t = time.time()
-    timings = {c: timer(*c) for c in candidates(fwd_grad, stride_fits)}
-    kernel, block, stride = pick(timings)
-    cache[key] = {"kernel": kernel, "block_size": block, "ckpt_stride": stride,
-                  "ms": {"%s/%d/S%d" % c: v for c, v in timings.items()}, "tuned_at": t}
+    timings = {c: timer(*c) for c in candidates(fwd_grad, stride_fits, small=n < SMALL_ENSEMBLE)}
+    kernel, block, lanes, stride = pick(timings)
+    cache[key] = {"kernel": kernel, "block_size": block, "warp_lanes": lanes, "ckpt_stride": stride,
+                  "ms": {"%s/%d/L%d/S%d" % c: v for c, v in timings.items()}, "tuned_at": t}
     save_cache(cache, cache_path)
-    return Choice(kernel, block, stride)
+    return Choice(kernel, block, lanes, stride)
 
 
 def share_sms(pieces, sm_count=None, reps=2):

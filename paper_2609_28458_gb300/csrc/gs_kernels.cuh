@@ -26,21 +26,32 @@ struct LaunchCfg {
 };
 
 // Resident 128-thread blocks per SM requested from the register allocator (__launch_bounds__), for
-// 7-stage pairs on states of at most 6 components: the FP32-pipe forward 5 blocks (96 registers and a
-// few spilled; measured on the 3 Gyr Milky-Way ensemble against 4 blocks at 128 registers: 1% faster
-// with the tape, 2% without; 6 blocks 42% slower), the FP64-control forward 4, the FP32 reverse 3
-// (<= 168; 2 blocks is 15% slower, 4 blocks 5%), without spills. FP64, Verner 7 and the 9-component
-// precession state keep the compiler's choice.
+// 7-stage pairs on states of at most 6 components: the FP32-pipe forward 4 (128 registers; measured on
+// the 3 Gyr Milky-Way ensemble with the explicit fused multiply-adds of the stage sums: forward 28.1 ms
+// against 30.7 ms at 5 blocks, where 96 registers spill; before those, 5 blocks had been 1-2% faster;
+// 6 blocks 42% slower), the FP64-control forward 4, the FP32 reverse 3 (<= 168; 2 blocks is 15%
+// slower, 4 blocks 5%), without spills. The FP64 forward of the 9-component
+// precession state 4 blocks (16 warps per SM at 128 registers, against 8 at the compiler's 255: the
+// FP64 pipe gets more warps to overlap; 10^6 Verner 7 solves 243.9 -> 222.5 ms despite spilling, 3
+// blocks 229.9 ms). Other FP64 and Verner 7 kernels keep the compiler's choice.
 #ifndef GS_FWD_BLOCKS_FP32DF
-#define GS_FWD_BLOCKS_FP32DF 5
+#define GS_FWD_BLOCKS_FP32DF 4
+#endif
+#ifndef GS_FWD_BLOCKS_FP32
+#define GS_FWD_BLOCKS_FP32 4
 #endif
 #ifndef GS_REV_BLOCKS_FP32
 #define GS_REV_BLOCKS_FP32 3
 #endif
+#ifndef GS_FWD_BLOCKS_FP64_D9
+#define GS_FWD_BLOCKS_FP64_D9 4
+#endif
 template <template <class> class SysT, class Tab, int PM, int MT = 0>
 struct Occupancy {
   static constexpr bool small = Tab::S <= 7 && SysT<float>::D <= 6 && MT == 0;
-  static constexpr int fwd = (PM == 2 && small) ? GS_FWD_BLOCKS_FP32DF : (PM == 1 && small) ? 4 : 1;
+  static constexpr int fwd = (PM == 2 && small) ? GS_FWD_BLOCKS_FP32DF
+                             : (PM == 1 && small) ? GS_FWD_BLOCKS_FP32
+                             : (PM == 0 && SysT<float>::D == 9 && MT == 0) ? GS_FWD_BLOCKS_FP64_D9 : 1;
   static constexpr int rev = ((PM == 1 || PM == 2) && small) ? GS_REV_BLOCKS_FP32 : 1;
 };
 

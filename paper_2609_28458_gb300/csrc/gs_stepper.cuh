@@ -144,10 +144,13 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
 
 constexpr float kEps48 = 3.5527136788005009e-15f;  // 2^-48: unit roundoff of an FP32 pair
 
-// a * b + c with one rounding, as an explicit fused multiply-add. The stage combinations and state
-// updates are written with it, so that every kernel that inlines them (the forward attempt, and the
+// a * b + c with one rounding, as an explicit fused multiply-add. The stage sums and state updates of
+// a step are written with it, so that every kernel that inlines them (the forward attempt, and the
 // reverse pass's replay of a checkpoint segment) rounds them alike, whichever multiply-add fusions the
-// compiler would otherwise pick in each (a product shared by two sums may be fused into one or both).
+// compiler would otherwise pick in each: a product that two sums share (for FSAL pairs the last
+// stage's weights are the new state's) may be rounded once and reused in one kernel and fused into
+// both sums in another. (Measured: with plain expressions the FP32-pair replay missed the next
+// checkpoint at 17% of segment ends; with these, at none.)
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ F2 fmadd(const F2& a, const F2& b, const F2& c) { return a * b + c; }
@@ -258,6 +261,8 @@ struct Traj {
   T p[NPP];
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
   double rem_c, hmin_c;  // PM 0, 1: (t1 - t) + tc and 16 eps max(|t|, |t1|), updated when t is
+  double last_c;         // PM 1: the step length from which the step is the last (rem_c, 8 ulp less)
+  double dk_c;           // PM 1: (sv - t) + tc of the pending output, with t
   float th, tl, hf, t1h, t1l, svh, svl;   // PM 2, 3
   float atolf, rtolf, lerr_prev;          // PM 1, 2, 3
   long long n;
@@ -328,6 +333,7 @@ struct Traj {
       sv_ok = save_valid(pb, n, kk, t0, t1);
       sv = save_at(pb, n, kk);
       if constexpr (DF) split_df(sv, svh, svl);
+      if constexpr (F32 && !DF) dk_c = pending_dk();  // (t, tc, rem_c unchanged since time_cache())
     }
   }
 
@@ -369,11 +375,12 @@ struct Traj {
     return hh;
   }
 
-  // PM 2: the same starting-step heuristic with FP32 norms, ratio and power, so that starting a
-  // trajectory issues no FP64 arithmetic beyond splitting its inputs (on GB300 an FP64 instruction
-  // costs 64 FP32 ones, and the lanes of a warp wait while one of them starts its trajectory).
-  // (th, tl) must hold t0.
-  __device__ float initial_step_f() {
+  // FP32-stage modes: the same starting-step heuristic with FP32 norms, ratio and power, so that
+  // starting a trajectory issues no FP64 arithmetic beyond splitting its inputs (on GB300 an FP64
+  // instruction costs 64 FP32 ones, and the lanes of a warp wait while one of them starts its
+  // trajectory: in a persistent warp some lane starts one every few attempts). tstart: t0 in the
+  // stage precision.
+  __device__ float initial_step_f(R tstart) {
     float sc[D];
     float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
@@ -396,7 +403,7 @@ struct Traj {
       if constexpr (DD) y1[i] = y[i] + R(h0) * k1[i];
       else y1[i] = y[i] + (ylo[i] + h0 * k1[i]);
     }
-    Sys::f((R(th) + R(tl)) + R(h0), y1, p, f1);
+    Sys::f(tstart + R(h0), y1, p, f1);
     float d2 = 0.0f;
 #pragma unroll
     for (int i = 0; i < D; i++) {
@@ -477,10 +484,11 @@ struct Traj {
         else if (k < kk) pb.tape.emit[n * pb.K + k] = kEmitT0;
       }
     }
-    load_sv(pb);
-    Sys::f(stage_time(t0), y, p, k1);
     t = t0;
     tc = 0.0;
+    rem_c = t1 - t0;
+    load_sv(pb);
+    Sys::f(stage_time(t0), y, p, k1);
     time_cache();
     err_prev = 1.0;
     lerr_prev = 0.0f;
@@ -489,8 +497,10 @@ struct Traj {
     if constexpr (DF) {
       split_df(t0, th, tl);
       split_df(t1, t1h, t1l);
-      hf = pb.h0 > 0.0 ? float(pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step_f();
+      hf = pb.h0 > 0.0 ? float(pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step_f(R(th) + R(tl));
       h = double(hf);
+    } else if constexpr (F32) {
+      h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : widen_f32(initial_step_f(R(t0)));
     } else {
       h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step(pb);
     }
@@ -770,11 +780,30 @@ struct Traj {
   // the quantities of the step-length tests that change only with the time (PM 0, 1): the remaining
   // interval and the step-size floor of the underflow test
   __device__ __forceinline__ void time_cache() {
-    if constexpr (!DF) {
+    if constexpr (F32 && !DF) {
+      // PM 1: the same quantities with integer instructions wherever the FP64 pipe is not needed:
+      // |t|, |t1| and their maximum on the bit patterns; 16 eps tm = tm 2^-48 by the exponent field;
+      // the last-step threshold eight units in the last place below the remainder (rem (1 - 2^-50)
+      // lies 4 to 8 units below it)
+      rem_c = (t1 - t) + tc;
+      const long long at = __double_as_longlong(t) & 0x7fffffffffffffffLL;
+      const long long a1 = __double_as_longlong(t1) & 0x7fffffffffffffffLL;
+      const long long tm = at > a1 ? at : a1;
+      const long long e48 = 48LL << 52;
+      hmin_c = __longlong_as_double(tm > e48 ? tm - e48 : 0LL);
+      const long long rb = __double_as_longlong(rem_c);
+      last_c = __longlong_as_double(rb > 8LL ? rb - 8LL : 0LL);
+      dk_c = pending_dk();
+    } else if constexpr (!DF) {
       rem_c = (t1 - t) + tc;
       const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
       hmin_c = 16.0 * DBL_EPSILON * tm;
     }
+  }
+  // PM 1: (sv - t) + tc of the pending output; for an output at t1 it is the remainder itself
+  __device__ __forceinline__ double pending_dk() const {
+    if (__double_as_longlong(sv) == __double_as_longlong(t1)) return rem_c;
+    return (sv - t) + tc;
   }
   // the time after an accepted step that is not the last (Kahan summation, or the error-free
   // advance of the FP32 time pair), then the next first stage of pairs without FSAL
@@ -835,6 +864,20 @@ struct Traj {
       // state one FP32 rounding of the step short of t1, far above df64's resolution)
       if constexpr (DD)
         if (last) hr = (R(t1h) + R(t1l)) - (R(th) + R(tl));
+    } else if constexpr (F32) {
+      // PM 1: the same tests against the cached thresholds, compared as bit patterns (the values
+      // are non-negative, NaN apart), so that they take no slot of the FP64 pipe
+      if (__double_as_longlong(rem_c) <= 0LL) { close_interval(pb); return; }
+      if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+      if (isnan_f64_bits(h)) { fail(ST_H_UNDERFLOW | ST_NONFINITE); return; }
+      if (le_nonneg_f64(last_c, h)) {
+        h = rem_c;
+        last = true;
+      } else if (!le_nonneg_f64(hmin_c, h)) {
+        fail(ST_H_UNDERFLOW);
+        return;
+      }
+      hr = R(h);
     } else {
       if (rem_c <= 0.0) { close_interval(pb); return; }
       if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
@@ -937,6 +980,9 @@ struct Traj {
         if constexpr (DF) {
           at_end = last && svh == t1h && svl == t1l;
           inside = last || ((svh - th) + (svl - tl)) <= hf;
+        } else if constexpr (F32) {  // PM 1: h > 0, so the bit patterns order as the values
+          at_end = last && __double_as_longlong(sv) == __double_as_longlong(t1);
+          inside = last || __double_as_longlong(dk_c) <= __double_as_longlong(h);
         } else {
           at_end = last && sv == t1;
           inside = last || ((sv - t) + tc) <= h;
@@ -957,7 +1003,9 @@ struct Traj {
               sig = fminf(fmaxf(__fdividef((svh - th) + (svl - tl), hf), 0.0f), 1.0f);
             }
           } else {
-            double sg = ((sv - t) + tc) / h;
+            double sg;
+            if constexpr (F32) sg = dk_c / h;
+            else sg = ((sv - t) + tc) / h;
             if (sg > 1.0) sg = 1.0;
             if (sg < 0.0) sg = 0.0;
             sig = R(sg);

@@ -65,10 +65,11 @@ def test_autotuned_configuration_gives_identical_results(tmp_path):
     e = W.mw(n=20000, seed=90, t1=1000.0, rtol=1e-8)
     y0, pr = torch.as_tensor(e.y0, device=dev), torch.as_tensor(e.params, device=dev)
     t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
-    kernel, block, _ = autotune.tune("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp32df", sample=8192,
+    kernel, block, lanes, _ = autotune.tune("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp32df", sample=8192,
                                   cache_path=str(tmp_path / "c.json"))
-    assert (kernel, block) in autotune.CANDIDATES
-    a = api.solve("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp64", kernel=kernel, block_size=block)
+    assert (kernel, block) in autotune.CANDIDATES and lanes in autotune.LANES
+    a = api.solve("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp64", kernel=kernel, block_size=block,
+                  warp_lanes=lanes)
     b = api.solve("mw", y0, pr, t0, t1, sv, e.rtol, e.atol, precision="fp64", kernel="plain", block_size=128)
     torch.cuda.synchronize()
     same = (a["n_accept"] == b["n_accept"]) & (a["n_reject"] == b["n_reject"])

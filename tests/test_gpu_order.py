@@ -52,3 +52,33 @@ def test_vjp_results_do_not_depend_on_order():
     torch.cuda.synchronize()
     for k in ("dLdy0", "dLdparams", "y", "n_accept"):
         assert torch.equal(a[k], b[k]), k
+
+
+def test_fewer_lanes_per_warp_give_identical_results():
+    """gs_options.warp_lanes: the persistent kernels hand trajectories to that many lanes of each warp
+    only (the rest retire at once). The per-trajectory arithmetic is the same, so solutions, step
+    counts and gradients are bit for bit those of full warps, for forward, adjoint and sensitivities."""
+    ensure_built()
+    dev = torch.device("cuda")
+    e = W.isochrone(n=1000, seed=71)
+    y0 = torch.as_tensor(e.y0, device=dev)
+    w = torch.as_tensor(np.random.default_rng(2).normal(size=(e.n, e.saveat.shape[-1], 6)), device=dev)
+    ref_s = api.solve("isochrone", y0, None, e.t0, e.t1, e.saveat, e.rtol, e.atol, kernel="persistent")
+    ref_g = api.vjp("isochrone", y0, None, e.t0, e.t1, e.saveat, e.rtol, e.atol, w, kernel="persistent")
+    for lanes in (16, 8, 1):
+        s = api.solve("isochrone", y0, None, e.t0, e.t1, e.saveat, e.rtol, e.atol, kernel="persistent",
+                      warp_lanes=lanes)
+        g = api.vjp("isochrone", y0, None, e.t0, e.t1, e.saveat, e.rtol, e.atol, w, kernel="persistent",
+                    warp_lanes=lanes)
+        torch.cuda.synchronize()
+        for k in ("y", "status", "n_accept", "n_reject"):
+            assert torch.equal(s[k], ref_s[k]), (lanes, k)
+        assert torch.equal(g["dLdy0"], ref_g["dLdy0"]), lanes
+    m = W.mw(n=600, seed=72, t1=500.0)
+    dp = torch.zeros((m.n, 4, 1), dtype=torch.float64, device=dev)
+    dp[:, 3, 0] = 1.0
+    a = api.jvp("mw", torch.as_tensor(m.y0, device=dev), m.params, m.t0, m.t1, m.saveat, m.rtol, m.atol, dparams=dp)
+    b = api.jvp("mw", torch.as_tensor(m.y0, device=dev), m.params, m.t0, m.t1, m.saveat, m.rtol, m.atol, dparams=dp,
+                warp_lanes=8)
+    torch.cuda.synchronize()
+    assert torch.equal(a["S"], b["S"]) and torch.equal(a["y"], b["y"])
