@@ -92,11 +92,13 @@ def reverse_flops(system, method, d, accepted):
     return accepted * ((S - 1) * f + 2 * d * n_a + S * int(2.5 * f) + 2 * d * (n_a + n_b))
 
 
-# DRAM bytes per accepted step of the headline's reverse kernels, from one-pass ncu captures
-# (dram__bytes_read.sum + dram__bytes_write.sum) of the 262,144-orbit, 750-Myr case (a tape of a few
-# GB; profiles/), divided by that launch's accepted steps; the traffic is proportional to the
-# accepted steps, so it scales to the full launch. None: not yet captured for that kernel.
-REV_DRAM_BYTES_PER_STEP = {"fp32df": 53.1, "fp32": None, "fp64": None}
+# DRAM bytes per accepted step of the headline's kernels (forward recording the tape, reverse), from
+# one-pass ncu captures (dram__bytes_read.sum + dram__bytes_write.sum) of the 262,144-orbit, 750-Myr
+# case (a tape of a few GB; profiles/), divided by that launch's accepted steps; the traffic is
+# proportional to the accepted steps, so it scales to the full launch. None: not captured for that
+# kernel, or the kernel changed since.
+FWD_DRAM_BYTES_PER_STEP = {"fp32": 76.6, "fp32df": None, "fp64": None}
+REV_DRAM_BYTES_PER_STEP = {"fp32": 71.2, "fp32df": 53.1, "fp64": None}
 # Fallback peaks when the probe cannot run: FP32 from unit counts and clock (152 SMs x 128 FP32
 # lanes x 2 flop x 2.07 GHz); FP64 the nominal GB300 rate
 PEAK_FP32_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -471,7 +473,8 @@ def run_gpu(args):
         traffic = bps * n_acc if bps else None
     else:
         dom, flops, dur = "k_persist (forward + tape record, %s)" % HEAD_PREC, n_att * F_ATT_FWD, fk
-        traffic = None
+        bps = FWD_DRAM_BYTES_PER_STEP.get(HEAD_PREC)
+        traffic = bps * n_acc if bps else None
     achieved = flops / (dur / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": ctx.peak32, "unit": "TFLOP/s",
                 "frac": achieved / ctx.peak32, "traffic": traffic, "peak_source": ctx.peak_source,
@@ -660,7 +663,9 @@ def _solve_rows(ctx, system, e, rows, errfn, reps, grad_stride=None):
     t0, t1, sv = (torch.as_tensor(x, device=dev) for x in (e.t0, e.t1, e.saveat))
     K = e.saveat.shape[-1]
     out = []
-    for prec, kern, meth, rtol, atol, grad in rows:
+    for row_spec in rows:
+        prec, kern, meth, rtol, atol, grad = row_spec[:6]
+        row_stride = row_spec[6] if len(row_spec) > 6 else grad_stride
         kw = dict(method=meth, precision=prec, kernel=kern, max_steps=2_000_000,
                   order="natural" if kern == "plain" else "auto")
         f_ms, s = ctx.timed(lambda: api.solve(system, y0, pr, t0, t1, sv, rtol, atol, **kw), reps, 1)
@@ -673,7 +678,7 @@ def _solve_rows(ctx, system, e, rows, errfn, reps, grad_stride=None):
             row["fwd_frac_of_peak"] = ctx.frac(forward_flops(system, meth, d, att, acc), f_ms, prec)["frac"]
             row["peak_kind"] = "FP64" if prec == "fp64" else "FP32"
         if grad:
-            stride = grad_stride or autotune.pick_stride(system, e.n, s["n_accept"], prec,
+            stride = row_stride or autotune.pick_stride(system, e.n, s["n_accept"], prec,
                                                          budget_bytes=torch.cuda.mem_get_info(dev)[0] // 2,
                                                          kernel=kern, K=K)
             ws = api.Workspace(dev)
@@ -741,12 +746,15 @@ def _wl_precession(ctx, quick=True, paper=False):
 
     rows = [("fp64", "persistent", "vern7", 3.16e-9, 3.16e-9, True), ("fp64", "plain", "vern7", 3.16e-9, 3.16e-9, False),
             ("fp64", "persistent", "tsit5", 5.62e-10, 5.62e-10, False)]
-    if paper:
+    if paper:  # the gradient also with checkpoint stride 16: its tape is a sixth of stride 1's
         rows = [("fp64", "persistent", "vern7", 3.16e-9, 3.16e-9, True),
+                ("fp64", "persistent", "vern7", 3.16e-9, 3.16e-9, True, 16),
                 ("fp64", "persistent", "tsit5", 5.62e-10, 5.62e-10, False)]
     if not quick:
         rows += [("fp64", "plain", "tsit5", 5.62e-10, 5.62e-10, False)]
-    out = _solve_rows(ctx, "precession", e, rows, errfn, 2 if quick else 3)
+    # the paper's interval takes ~4 s forward and ~12 s forward + gradient per 10^6 solves: one timed
+    # repetition after the warm-up in the default run
+    out = _solve_rows(ctx, "precession", e, rows, errfn, (1 if paper else 2) if quick else 3)
     return {"config": "10^6 binary spin-precession solves (state 9, FP64), %s" %
                       ("the paper's interval r = 100 M -> 10 M (v = 0.1 -> 10^-1/2)" if paper else
                        "f = 20 Hz (GW) to v = 0.3; binaries above ~87 Msun have an empty interval"),

@@ -87,3 +87,44 @@ def test_noalloc_rejects_ensembles_beyond_its_scratch():
                                    fake, fake, fake, fake, fake, None)
     assert rc == _abi.GS_ERR_WORKSPACE
     assert "built-in scratch" in _abi.lib().gs_last_error().decode()
+
+
+def test_noalloc_limit_is_exactly_gs_vjps():
+    """The largest ensemble the built-in scratch accepts is the one whose part before the tape pool
+    plus one tape chunk fits it, as gs_vjp would require of a workspace of that size: the call just
+    inside the limit runs (every trajectory has an empty interval, so no tape is needed), the next size
+    is refused before any launch."""
+    ensure_built()
+    L = _abi.lib()
+    opt = _abi.options(kernel="persistent")
+    chunk = L.gs_tape_chunk_bytes(1, ctypes.byref(opt))
+
+    def need(n):
+        return L.gs_workspace_bytes(1, n, 1, ctypes.byref(opt), 1, 0.0) + chunk
+
+    lo, hi = 1, _abi.NOALLOC_SCRATCH_BYTES
+    while hi - lo > 1:  # largest n with need(n) <= the scratch
+        mid = (lo + hi) // 2
+        if need(mid) <= _abi.NOALLOC_SCRATCH_BYTES:
+            lo = mid
+        else:
+            hi = mid
+    n_in, n_out = lo, hi
+    dev = torch.device("cuda")
+    f64 = lambda *shape: torch.zeros(shape, dtype=torch.float64, device=dev)
+    i32 = lambda n: torch.zeros(n, dtype=torch.int32, device=dev)
+    y0, pr, t0, t1, sv, w = f64(n_out, 6), f64(n_out, 4), f64(n_out), f64(n_out), f64(1), f64(n_out, 1, 6)
+    pr[:, :3] = 1.0
+    pr[:, 3] = 1.0
+    gy, gp, y = f64(n_out, 6), f64(n_out, 4), f64(n_out, 1, 6)
+    st, na, nr = i32(n_out), i32(n_out), i32(n_out)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(n):
+        return L.gs_vjp_noalloc(1, n, _p(y0), _p(pr), _p(t0), _p(t1), 1e-6, 1e-6, 1, _p(sv), ctypes.byref(opt), _p(w),
+                                _p(gy), _p(gp), _p(y), _p(st), _p(na), _p(nr), stream)
+
+    assert call(n_out) == _abi.GS_ERR_WORKSPACE
+    assert call(n_in) == _abi.GS_OK
+    torch.cuda.synchronize()
+    assert bool((st[:n_in] == _abi.ST_EMPTY_INTERVAL).all())
