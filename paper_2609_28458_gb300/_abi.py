@@ -22,11 +22,12 @@ ST_FAILED = ST_MAX_STEPS | ST_H_UNDERFLOW | ST_NONFINITE | ST_TAPE_OVERFLOW
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_WORKSPACE = 0, 1, 2, 3
 
 EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_jvp", "gs_vjp_noalloc", "gs_workspace_bytes",
-           "gs_tape_chunk_bytes", "gs_alu_probe",
+           "gs_tape_chunk_bytes", "gs_alu_probe", "gs_selftest",
            "gs_solve_flat", "gs_flat_workspace_bytes", "gs_profile_default_options", "gs_profile_prep_bytes",
            "gs_profile_prepare", "gs_profile_workspace_bytes", "gs_profile_fit", "gs_rhs", "gs_last_error",
            "gs_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
+SELFTEST_CHECKS = 8  # GS_SELFTEST_CHECKS
 
 
 class GsOptions(ctypes.Structure):
@@ -115,6 +116,8 @@ def lib():
     L.gs_tape_chunk_bytes.restype = ctypes.c_size_t
     L.gs_alu_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_int64), _vp]
     L.gs_alu_probe.restype = ctypes.c_int
+    L.gs_selftest.argtypes = [ctypes.c_int64, ctypes.c_uint64, _vp, _vp]
+    L.gs_selftest.restype = ctypes.c_int
     L.gs_rhs.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.gs_rhs.restype = ctypes.c_int
     L.gs_last_error.argtypes = []

@@ -341,6 +341,20 @@ def alu_peak(fp64=False, iters=None, blocks_per_sm=4, device=None, reps=3, packe
     return 2.0 * cnt.value / (best / 1e3) / 1e12
 
 
+SELFTEST_NAMES = ("narrow_f64", "widen_f32", "le_f64", "eq_f64", "nan_finite", "sign_ops", "le_nonneg_f64",
+                  "log2_f64_f32")
+
+
+def selftest(n=1 << 22, seed=0, device=None):
+    """gs_selftest: the kernels' bit-level FP64 helpers against the instructions they replace, on the
+    device. Returns {check name: (mismatches, bit pattern of one mismatching input)}."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    counts = torch.zeros(2 * _abi.SELFTEST_CHECKS, dtype=torch.int64, device=dev)
+    _abi.check(_abi.lib().gs_selftest(int(n), int(seed), _ptr(counts), _stream(dev)))
+    c = [v & 0xFFFFFFFFFFFFFFFF for v in counts.cpu().tolist()]
+    return {name: (c[i], c[_abi.SELFTEST_CHECKS + i]) for i, name in enumerate(SELFTEST_NAMES)}
+
+
 class GsSolve(torch.autograd.Function):
     """y = solve(y0, params) with the discrete adjoint as backward (torch autograd wiring)."""
 

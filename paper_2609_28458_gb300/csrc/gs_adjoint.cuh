@@ -59,7 +59,7 @@ struct Adjoint {
   template <bool USE_SLAB = false>
   __device__ static void reverse_stages(const T& tr, double tt, double hh, R (*Y)[D], R (*kbar)[D], int jmax,
                                         R* ybar, PAcc& pacc, unsigned sl = 0, unsigned st = 0) {
-    const R hr = R(hh);
+    const R hr = T::cvt(hh);
     R gsum[NPA];
 #pragma unroll
     for (int q = 0; q < NPA; q++) gsum[q] = R(0);
@@ -161,7 +161,8 @@ struct Adjoint {
       v.tc = 0.0;
       v.h = double(v.hf);
     } else {
-      v.t = r.t0.x; v.tc = r.t0.y; v.h = r.t1.x; v.last = r.t1.y != 0.0;
+      v.t = r.t0.x; v.tc = r.t0.y; v.h = r.t1.x;
+      v.last = (__double_as_longlong(r.t1.y) << 1) != 0;  // the flag is 1.0 or 0.0: tested on its bits
     }
     return v;
   }
@@ -247,7 +248,7 @@ struct Adjoint {
     if (st & ST_EMPTY) { write_const(pb, 0.0, 0.0, true, false); done = true; return; }  // outputs are y0
     if (nrec == 0) { write_const(pb, 0.0, 0.0, true, true); done = true; return; }
 #pragma unroll
-    for (int q = 0; q < NP; q++) tr.p[q] = R(pb.params[n * NP + q]);
+    for (int q = 0; q < NP; q++) tr.p[q] = T::cvt(pb.params[n * NP + q]);
     if (NP == 0) tr.p[0] = R(0);
     prep_params<Sys>(tr.p);
 #pragma unroll
@@ -393,8 +394,8 @@ struct Adjoint {
       cur.tc = 0.0;
     } else {
       const double hv = reinterpret_cast<const double*>(base + kChunkHeader)[o];
-      cur.last = hv < 0.0;
-      cur.h = fabs(hv);
+      cur.last = signbit_f64_bits(hv);  // (the sign marks the last step; h > 0)
+      cur.h = abs_f64_bits(hv);
       cur.t = sta[i0];
       cur.tc = stb[i0];
     }
@@ -422,7 +423,7 @@ struct Adjoint {
 #pragma unroll
     for (int i = 0; i < D; i++) ydir[i] = R(0);
     bool used_last_stage = false;
-    const R hr = R(cur.h);
+    const R hr = T::cvt(cur.h);
     while (kk >= 0) {
       if (em[kk] == kEmitUnused) { kk--; continue; }
       if (em[kk] != a) break;
@@ -529,7 +530,7 @@ struct Adjoint {
 #pragma unroll
     for (int i = 0; i < D; i++) ydir[i] = R(0);
     bool used_last_stage = false;
-    const R hr = R(cur.h);
+    const R hr = T::cvt(cur.h);
     // output cotangents of this step, latest first
     while (kk >= 0) {
       if (!save_valid(pb, n, kk, t0, t1)) { kk--; continue; }

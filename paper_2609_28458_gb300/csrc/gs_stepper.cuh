@@ -32,6 +32,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "gs_bits.cuh"
 #include "gs_dual.cuh"
 #include "gs_systems.cuh"
 #include "gs_tableaux.cuh"
@@ -123,10 +124,16 @@ __device__ __forceinline__ double save_at(const Problem& pb, long long n, int k)
   return pb.per_traj ? pb.saveat[n * pb.K + k] : pb.saveat[k];
 }
 
-// An output time is used iff it lies in [t0, t1] and does not decrease.
+// An output time is used iff it lies in [t0, t1] and does not decrease (t0, t1 finite).
+// save_valid_bits: the same answer from the bit patterns (gs_bits.cuh), for trajectory start-up in the
+// FP32-stage mode.
 __device__ __forceinline__ bool save_valid(const Problem& pb, long long n, int k, double t0, double t1) {
   const double s = save_at(pb, n, k);
   return s >= t0 && s <= t1 && (k == 0 || s >= save_at(pb, n, k - 1));
+}
+__device__ __forceinline__ bool save_valid_bits(const Problem& pb, long long n, int k, double t0, double t1) {
+  const double s = save_at(pb, n, k);
+  return le_f64_bits(t0, s) && le_f64_bits(s, t1) && (k == 0 || le_f64_bits(save_at(pb, n, k - 1), s));
 }
 
 template <class R>
@@ -154,32 +161,6 @@ constexpr float kEps48 = 3.5527136788005009e-15f;  // 2^-48: unit roundoff of an
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ F2 fmadd(const F2& a, const F2& b, const F2& c) { return a * b + c; }
-// An FP32 number widened to FP64 exactly by moving its bits (sign; exponent rebiased by 1023 - 127;
-// mantissa shifted up by 29) with integer instructions, where a conversion instruction would take a
-// slot of the FP64 pipe, which GB300 runs at 1/64 of the FP32 rate. Zero (and, with flush-to-zero, a
-// subnormal) gives zero; infinities and NaNs keep their class.
-__device__ __forceinline__ double widen_f32(float f) {
-  const uint32_t u = __float_as_uint(f);
-  const uint32_t sgn = u & 0x80000000u, ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
-  uint32_t hi = sgn | ((ex + 896u) << 20) | (man >> 3), lo = man << 29;
-  if (ex == 0u) { hi = sgn; lo = 0u; }
-  if (ex == 0xffu) hi = sgn | 0x7ff00000u | (man >> 3) | (man ? 0x80000u : 0u);
-  return __hiloint2double(int(hi), int(lo));
-}
-// Order, NaN test and log2 of a non-negative FP64 number (a sum of squares) from its bits with
-// integer and FP32 instructions: for x, y >= 0 the bit patterns order as the values do, and every
-// NaN pattern lies above that of +inf.
-__device__ __forceinline__ bool le_nonneg_f64(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
-__device__ __forceinline__ bool isnan_f64_bits(double x) {
-  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
-}
-// log2 x to FP32 accuracy: the unbiased exponent plus log2 of the mantissa truncated to 24 bits
-__device__ __forceinline__ float log2_f64_f32(double x) {
-  const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
-  const int ex = int((hi >> 20) & 0x7ffu) - 1023;
-  const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
-  return float(ex) + __log2f(m);
-}
 template <class R, int M>
 __device__ __forceinline__ Dual<R, M> fmadd(R a, const Dual<R, M>& b, const Dual<R, M>& c) {
   Dual<R, M> r;
@@ -223,6 +204,10 @@ struct Traj {
   static constexpr bool F32 = PrecTraits<PM>::F32;
   static constexpr bool DF = PrecTraits<PM>::DF;
   static constexpr bool DD = PrecTraits<PM>::DD;
+  // PM 1 keeps FP64 numbers beside FP32 stages; its conversions between the two and its tests of
+  // FP64 inputs go through the integer helpers of gs_bits.cuh, so that the FP64 pipe carries only the
+  // FP64 arithmetic of the precision split (the other modes use the instructions)
+  static constexpr bool BITS = PM == 1;
   using R = typename PrecTraits<PM>::R;
   using T = typename std::conditional<(MT > 0), Dual<R, (MT > 0 ? MT : 1)>, R>::type;
   using Sys = SysT<T>;
@@ -262,14 +247,18 @@ struct Traj {
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
   double rem_c, hmin_c;  // PM 0, 1: (t1 - t) + tc and 16 eps max(|t|, |t1|), updated when t is
   double last_c;         // PM 1: the step length from which the step is the last (rem_c, 8 ulp less)
-  double dk_c;           // PM 1: (sv - t) + tc of the pending output, with t
+  int32_t kend;          // PM 1: outputs kend.. are all at t1 (or unused): none is due before the last step
   float th, tl, hf, t1h, t1l, svh, svl;   // PM 2, 3
   float atolf, rtolf, lerr_prev;          // PM 1, 2, 3
   long long n;
   int32_t kk, nacc, nrej, status, chunk;
   bool done, failed, rec_ok, sv_ok;
 
-  __device__ __forceinline__ R stage_time(double ts) const { return R(ts); }
+  __device__ __forceinline__ static R cvt(double x) {
+    if constexpr (BITS) return narrow_f64(x);
+    else return R(x);
+  }
+  __device__ __forceinline__ R stage_time(double ts) const { return cvt(ts); }
 
   __device__ __forceinline__ double yval(int i) const {
     if constexpr (F32) return double(val(y[i])) + double(ylo[i]);
@@ -333,7 +322,6 @@ struct Traj {
       sv_ok = save_valid(pb, n, kk, t0, t1);
       sv = save_at(pb, n, kk);
       if constexpr (DF) split_df(sv, svh, svl);
-      if constexpr (F32 && !DF) dk_c = pending_dk();  // (t, tc, rem_c unchanged since time_cache())
     }
   }
 
@@ -379,8 +367,8 @@ struct Traj {
   // starting a trajectory issues no FP64 arithmetic beyond splitting its inputs (on GB300 an FP64
   // instruction costs 64 FP32 ones, and the lanes of a warp wait while one of them starts its
   // trajectory: in a persistent warp some lane starts one every few attempts). tstart: t0 in the
-  // stage precision.
-  __device__ float initial_step_f(R tstart) {
+  // stage precision; span: t1 - t0 in FP32.
+  __device__ float initial_step_f(R tstart, float span) {
     float sc[D];
     float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
@@ -394,7 +382,6 @@ struct Traj {
     }
     d0 = sqrtf(d0 / D);
     d1 = sqrtf(d1 / D);
-    const float span = float(t1 - t0);
     float h0 = (d0 < 1e-5f || d1 < 1e-5f) ? 1e-6f : 0.01f * (d0 / d1);
     h0 = fminf(h0, span);
     T y1[D], f1[D];
@@ -422,13 +409,27 @@ struct Traj {
     done = false; failed = false; rec_ok = true; chunk = -1; sv_ok = false;
     t0 = pb.t0[n];
     t1 = pb.t1[n];
-    bool fin = isfinite(t0) && isfinite(t1);
+    // (PM 1: tests and conversions on the bit patterns; a lane of a persistent warp starts a
+    // trajectory alone, and each FP64-pipe instruction would cost the warp's whole share of the pipe)
+    const auto finite = [](double x) {
+      if constexpr (BITS) return isfinite_f64_bits(x);
+      else return bool(isfinite(x));
+    };
+    const auto valid = [&](int k) {
+      if constexpr (BITS) return save_valid_bits(pb, n, k, t0, t1);
+      else return save_valid(pb, n, k, t0, t1);
+    };
+    bool fin = finite(t0) && finite(t1);
     double y0d[D];
 #pragma unroll
     for (int i = 0; i < D; i++) {
       y0d[i] = pb.y0[n * D + i];
-      fin = fin && isfinite(y0d[i]);
-      if constexpr (F32) {
+      fin = fin && finite(y0d[i]);
+      if constexpr (BITS) {
+        const float hi = narrow_f64(y0d[i]);
+        y[i] = T(hi);
+        ylo[i] = narrow_f64(y0d[i] - widen_f32(hi));
+      } else if constexpr (F32) {
         const float hi = float(y0d[i]);
         y[i] = T(hi);
         ylo[i] = float(y0d[i] - double(hi));
@@ -439,8 +440,8 @@ struct Traj {
 #pragma unroll
     for (int q = 0; q < NP; q++) {
       const double pv = pb.params[n * NP + q];
-      fin = fin && isfinite(pv);
-      p[q] = T(R(pv));
+      fin = fin && finite(pv);
+      p[q] = T(cvt(pv));
     }
     if (NP == 0) p[0] = T(R(0));
     if constexpr (MT > 0) {  // sensitivity seeds: S(t0) = dy0, parameter directions dtheta
@@ -462,25 +463,35 @@ struct Traj {
       done = true;
       return;
     }
-    if (!(t1 > t0)) {  // empty or reversed interval: every output is y0 (and S = dy0)
+    bool empty;
+    if constexpr (BITS) empty = le_f64_bits(t1, t0);
+    else empty = !(t1 > t0);
+    if (empty) {  // empty or reversed interval: every output is y0 (and S = dy0)
       status = ST_EMPTY;
       for (int k = 0; k < pb.K; k++) write_y0(pb, k, y0d);
       done = true;
       return;
     }
+    if constexpr (BITS) kend = 0;
     for (int k = 0; k < pb.K; k++) {
-      if (!save_valid(pb, n, k, t0, t1)) {
+      if (!valid(k)) {
         status |= ST_SAVEAT_OUTSIDE;
         write_nan(pb, k);
+      } else if constexpr (BITS) {
+        if (!eq_f64_bits(save_at(pb, n, k), t1)) kend = k + 1;
       }
     }
-    while (kk < pb.K && (!save_valid(pb, n, kk, t0, t1) || save_at(pb, n, kk) == t0)) {
-      if (save_valid(pb, n, kk, t0, t1)) write_y0(pb, kk, y0d);
+    const auto at_t0 = [&](int k) {
+      if constexpr (BITS) return eq_f64_bits(save_at(pb, n, k), t0);
+      else return save_at(pb, n, k) == t0;
+    };
+    while (kk < pb.K && (!valid(kk) || at_t0(kk))) {
+      if (valid(kk)) write_y0(pb, kk, y0d);
       kk++;
     }
     if (pb.tape.emit) {  // checkpointed tape: outputs at t0 and unused ones are known now
       for (int k = 0; k < pb.K; k++) {
-        if (!save_valid(pb, n, k, t0, t1)) pb.tape.emit[n * pb.K + k] = kEmitUnused;
+        if (!valid(k)) pb.tape.emit[n * pb.K + k] = kEmitUnused;
         else if (k < kk) pb.tape.emit[n * pb.K + k] = kEmitT0;
       }
     }
@@ -492,16 +503,25 @@ struct Traj {
     time_cache();
     err_prev = 1.0;
     lerr_prev = 0.0f;
-    atolf = float(pb.atol);
-    rtolf = float(pb.rtol);
-    if constexpr (DF) {
+    if constexpr (BITS) {
+      atolf = narrow_f64(pb.atol);
+      rtolf = narrow_f64(pb.rtol);
+      // the caller's first step (h0 > 0) at most the interval, else the starting-step heuristic;
+      // rem_c = t1 - t0 > 0 here
+      const long long hb = __double_as_longlong(pb.h0);
+      const bool given = hb > 0LL && hb <= 0x7ff0000000000000LL;
+      h = given ? (le_nonneg_f64(pb.h0, rem_c) ? pb.h0 : rem_c)
+                : widen_f32(initial_step_f(narrow_f64(t0), narrow_f64(rem_c)));
+    } else if constexpr (DF) {
+      atolf = float(pb.atol);
+      rtolf = float(pb.rtol);
       split_df(t0, th, tl);
       split_df(t1, t1h, t1l);
-      hf = pb.h0 > 0.0 ? float(pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step_f(R(th) + R(tl));
+      hf = pb.h0 > 0.0 ? float(pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step_f(R(th) + R(tl), float(t1 - t0));
       h = double(hf);
-    } else if constexpr (F32) {
-      h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : widen_f32(initial_step_f(R(t0)));
     } else {
+      atolf = float(pb.atol);
+      rtolf = float(pb.rtol);
       h = pb.h0 > 0.0 ? (pb.h0 < t1 - t0 ? pb.h0 : t1 - t0) : initial_step(pb);
     }
   }
@@ -512,7 +532,7 @@ struct Traj {
   template <bool SAVE = false>
   __device__ __forceinline__ void stages(double tt, double hh, T (*k)[D], T (*Y)[D], int nst, unsigned sl = 0,
                                          unsigned st = 0) const {
-    const R hr = R(hh);
+    const R hr = cvt(hh);
 #pragma unroll
     for (int i = 0; i < D; i++) { k[0][i] = k1[i]; if (Y) Y[0][i] = y[i]; }
 #pragma unroll
@@ -650,7 +670,7 @@ struct Traj {
   __device__ void record_ck(const Problem& pb, int o, int a, bool last) {
     unsigned char* base = pb.tape.pool + (long long)chunk * pb.tape.chunk_bytes;
     if constexpr (DF) reinterpret_cast<float*>(base + kChunkHeader)[o] = last ? -hf : hf;
-    else reinterpret_cast<double*>(base + kChunkHeader)[o] = last ? -h : h;
+    else reinterpret_cast<double*>(base + kChunkHeader)[o] = last ? neg_f64_bits(h) : h;
     if (a % pb.tape.stride != 0) return;
     uint32_t w[kCkWords];
     if constexpr (F32) {
@@ -793,7 +813,6 @@ struct Traj {
       hmin_c = __longlong_as_double(tm > e48 ? tm - e48 : 0LL);
       const long long rb = __double_as_longlong(rem_c);
       last_c = __longlong_as_double(rb > 8LL ? rb - 8LL : 0LL);
-      dk_c = pending_dk();
     } else if constexpr (!DF) {
       rem_c = (t1 - t) + tc;
       const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
@@ -833,7 +852,7 @@ struct Traj {
       hr = hf;
     } else {
       h = hrec;
-      hr = R(h);
+      hr = cvt(h);
     }
     T k[S][D];
     T ynew[D];
@@ -877,7 +896,7 @@ struct Traj {
         fail(ST_H_UNDERFLOW);
         return;
       }
-      hr = R(h);
+      hr = cvt(h);
     } else {
       if (rem_c <= 0.0) { close_interval(pb); return; }
       if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
@@ -973,16 +992,22 @@ struct Traj {
     if (accept) {
       nacc += 1;
       if (pb.record) record_slot(pb, last, hr);
-      // ---- outputs inside (t, t + h] (Eq. dense), or the new state itself at t1
-      while (kk < pb.K) {
+      // ---- outputs inside (t, t + h] (Eq. dense), or the new state itself at t1. PM 1 skips the
+      // scan while every pending output is at t1 and the step is not the last (an integer test; the
+      // FP64 distance to the pending output is formed only where an output may be due)
+      bool scan = true;
+      if constexpr (BITS) scan = last || kk < kend;
+      while (scan && kk < pb.K) {
         if (!sv_ok) { kk++; load_sv(pb); continue; }
         bool at_end, inside;
+        double dk = 0.0;
         if constexpr (DF) {
           at_end = last && svh == t1h && svl == t1l;
           inside = last || ((svh - th) + (svl - tl)) <= hf;
         } else if constexpr (F32) {  // PM 1: h > 0, so the bit patterns order as the values
           at_end = last && __double_as_longlong(sv) == __double_as_longlong(t1);
-          inside = last || __double_as_longlong(dk_c) <= __double_as_longlong(h);
+          dk = pending_dk();
+          inside = last || __double_as_longlong(dk) <= __double_as_longlong(h);
         } else {
           at_end = last && sv == t1;
           inside = last || ((sv - t) + tc) <= h;
@@ -1004,7 +1029,7 @@ struct Traj {
             }
           } else {
             double sg;
-            if constexpr (F32) sg = dk_c / h;
+            if constexpr (F32) sg = dk / h;
             else sg = ((sv - t) + tc) / h;
             if (sg > 1.0) sg = 1.0;
             if (sg < 0.0) sg = 0.0;

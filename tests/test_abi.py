@@ -181,3 +181,14 @@ def test_noalloc_checks_the_system_first(lib):
     rc = lib.gs_vjp_noalloc(42, 1 << 30, fake, fake, fake, fake, 1e-6, 1e-6, 1, fake, ctypes.byref(o), fake, fake,
                             fake, fake, fake, fake, fake, None)
     assert rc == _abi.GS_ERR_INVALID and "unknown system" in lib.gs_last_error().decode()
+
+
+def test_selftest_entry_checks_arguments_on_the_host(lib):
+    """gs_selftest's check count matches the binding's, and bad arguments are refused before any CUDA
+    call (the device run itself is tests/test_gpu_bits.py)."""
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    assert int(re.search(r"#define GS_SELFTEST_CHECKS (\d+)", src).group(1)) == _abi.SELFTEST_CHECKS
+    from paper_2609_28458_gb300 import api
+    assert len(api.SELFTEST_NAMES) == _abi.SELFTEST_CHECKS
+    assert lib.gs_selftest(0, 0, None, None) == _abi.GS_ERR_INVALID
+    assert lib.gs_selftest(16, 0, None, None) == _abi.GS_ERR_INVALID
