@@ -216,8 +216,10 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
  * it: make that first call before any stream capture. Calls share the array and it keeps the last
  * call's contents (the call clears what must start at zero); calls that overlap on the GPU race, so
  * issue them one after another. An ensemble whose part before the tape pool
- * (gs_workspace_bytes(system, N, K, opt, 1, 0): 16 N bytes of per-trajectory arrays, padded, the
- * 256-byte header, 16 KB of counters, and 4 N K bytes with a checkpoint stride above 1) plus one
+ * (gs_workspace_bytes(system, N, K, opt, 1, 0): 16 N bytes of per-trajectory arrays and the
+ * prepared-start rows of the persistent forward (112 to 256 bytes per trajectory by system and
+ * precision), padded, the 256-byte header, 16 KB of counters, and 4 N K bytes with a checkpoint
+ * stride above 1) plus one
  * tape chunk (gs_tape_chunk_bytes) exceeds the array is rejected with GS_ERR_WORKSPACE (an unknown
  * system with GS_ERR_INVALID first); trajectories whose steps do not fit in the rest of the array
  * get GS_ST_TAPE_OVERFLOW and NaN gradients. A checkpoint stride above 1 fits about S times more
@@ -227,9 +229,13 @@ int gs_vjp_noalloc(int32_t system, int64_t N, const double* y0, const double* pa
                    const gs_options* opt, const double* dLdy, double* dLdy0, double* dLdparams,
                    double* y_out, int32_t* status, int32_t* n_accept, int32_t* n_reject, void* cuda_stream);
 
-/* Workspace bytes for N trajectories. for_vjp = 0: the work counters and the longest-first work
- * list (order[N], bucket counters, cost[N]); a smaller workspace runs GS_ORDER_AUTO in stored order
- * and rejects GS_ORDER_ESTIMATE and GS_ORDER_HINT with GS_ERR_WORKSPACE.
+/* Workspace bytes for N trajectories. for_vjp = 0: the work counters, the longest-first work list
+ * (order[N], bucket counters, cost[N]) and the prepared starts of the persistent forward (one row
+ * per trajectory: its state after start-up, written by a one-thread-per-trajectory pass so that a
+ * lane of a persistent warp that takes a new trajectory loads it instead of starting it while the
+ * other lanes wait; not for GS_DF64). A smaller workspace runs GS_ORDER_AUTO in stored order and
+ * starts trajectories in place, and rejects GS_ORDER_ESTIMATE and GS_ORDER_HINT with
+ * GS_ERR_WORKSPACE.
  * for_vjp != 0: room for a step tape of `steps_hint` accepted steps per trajectory on average
  * (rounded up to whole chunks per trajectory, plus one), in the chunk size of opt->precision and
  * opt->ckpt_stride (FP64, stride 1 when opt is NULL). With steps_hint = 0: the part before the tape

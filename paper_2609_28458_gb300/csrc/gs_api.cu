@@ -70,12 +70,22 @@ int32_t stride_of(const gs_options* opt) { return (opt && opt->ckpt_stride > 1) 
 
 // workspace: header (work counters), head[N], n_rec[N], a work list order[N] with its bucket
 // counters and the estimated costs cost[N] (longest-first ordering of the forward and reverse
-// launches) [= total_fixed], with a checkpoint stride above 1 the output attribution emit[N, K],
-// then the tape pool
+// launches), the prepared starts of the persistent forward start[N] (rows of start_row bytes)
+// [= total_fixed], with a checkpoint stride above 1 the output attribution emit[N, K], then the
+// tape pool
 struct Layout {
-  size_t header, head, nrec, order, buckets, cost, total_fixed, emit, pool;
+  size_t header, head, nrec, order, buckets, cost, start, total_fixed, emit, pool;
 };
-Layout layout(int64_t N, int32_t K = 0, int32_t stride = 1) {
+long long start_row(int32_t system, int32_t precision) {
+  switch (system) {
+    case GS_SYS_ISOCHRONE: return gs::start_row_isochrone(precision);
+    case GS_SYS_MW: return gs::start_row_mw(precision);
+    case GS_SYS_PRECESSION: return gs::start_row_precession(precision);
+    case GS_SYS_QUINTESSENCE: return gs::start_row_quintessence(precision);
+    default: return gs::start_row_loghalo(precision);
+  }
+}
+Layout layout(int64_t N, int32_t K, int32_t stride, long long row) {
   Layout L;
   L.header = 0;
   L.head = 256;
@@ -83,7 +93,8 @@ Layout layout(int64_t N, int32_t K = 0, int32_t stride = 1) {
   L.order = L.nrec + align256(size_t(N) * 4);
   L.buckets = L.order + align256(size_t(N) * 4);
   L.cost = L.buckets + align256(size_t(gs::kOrderBuckets) * 4);
-  L.total_fixed = L.cost + align256(size_t(N) * 4);
+  L.start = L.cost + align256(size_t(N) * 4);
+  L.total_fixed = L.start + align256(size_t(N) * size_t(row));
   L.emit = L.total_fixed;
   L.pool = L.emit + (stride > 1 ? align256(size_t(N) * size_t(K > 0 ? K : 0) * 4) : 0);
   return L;
@@ -91,8 +102,8 @@ Layout layout(int64_t N, int32_t K = 0, int32_t stride = 1) {
 
 // Ordering of a forward launch (gs_options.order): the work list needs the workspace's fixed part.
 // (order and cost_hint are validated by check_common)
-int set_order(gs::Problem& pb, const gs_options* opt, int64_t N, void* ws, size_t ws_bytes) {
-  const Layout L = layout(N);
+int set_order(gs::Problem& pb, const gs_options* opt, int64_t N, void* ws, size_t ws_bytes, long long row) {
+  const Layout L = layout(N, 0, 1, row);
   bool use = false;
   if (opt->order == GS_ORDER_HINT || opt->order == GS_ORDER_ESTIMATE) use = true;
   if (opt->order == GS_ORDER_AUTO) use = opt->cost_hint != nullptr || N >= 32768;
@@ -108,6 +119,16 @@ int set_order(gs::Problem& pb, const gs_options* opt, int64_t N, void* ws, size_
   pb.ord_order = reinterpret_cast<int32_t*>(base + L.order);
   pb.ord_cnt = reinterpret_cast<unsigned int*>(base + L.buckets);
   return GS_OK;
+}
+
+// Prepared starts of a persistent forward launch (modes 0-2): when the workspace holds the fixed part,
+// else the persistent kernel starts trajectories in place.
+void set_start(gs::Problem& pb, int kernel, int64_t N, void* ws, size_t ws_bytes, long long row) {
+  if (kernel != GS_KERNEL_PERSISTENT || row <= 0 || !ws) return;
+  const Layout L = layout(N, 0, 1, row);
+  if (ws_bytes < L.total_fixed) return;
+  pb.start = static_cast<unsigned char*>(ws) + L.start;
+  pb.start_row = row;
 }
 
 
@@ -206,14 +227,15 @@ gs::Problem make_problem(int64_t N, const double* y0, const double* params, cons
   return pb;
 }
 
-int set_tape(gs::Problem& pb, int32_t d, const gs_options* opt, int64_t N, int32_t K, void* ws, size_t ws_bytes) {
+int set_tape(gs::Problem& pb, int32_t d, const gs_options* opt, int64_t N, int32_t K, void* ws, size_t ws_bytes,
+             long long row) {
   if (opt->tape_capacity <= 0) return fail(GS_ERR_INVALID, "tape_capacity must be positive");
   const int32_t stride = stride_of(opt);
   if (stride > 1 && opt->precision == GS_DF64)
     return fail(GS_ERR_INVALID, "checkpoint strides above 1 are not available in GS_DF64");
   if (stride > 1 && opt->kernel == GS_KERNEL_PLAIN)
     return fail(GS_ERR_INVALID, "checkpoint strides above 1 run in the persistent kernels (kernel auto or persistent)");
-  Layout L = layout(N, K, stride);
+  Layout L = layout(N, K, stride, row);
   const long long cb = chunk_bytes(d, opt->precision, stride);
   if (!ws) return fail(GS_ERR_WORKSPACE, "this call needs a workspace (see gs_workspace_bytes)");
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(GS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -277,7 +299,7 @@ size_t gs_workspace_bytes(int32_t system, int64_t N, int32_t K, const gs_options
   int32_t d, p;
   if (dims_of(system, &d, &p) || N < 0 || K < 0) return 0;
   const int32_t stride = stride_of(opt);
-  Layout L = layout(N, K, stride);
+  Layout L = layout(N, K, stride, start_row(system, opt ? opt->precision : GS_FP64));
   if (!for_vjp) return L.total_fixed;
   if (!(steps_hint > 0.0)) return L.pool;
   const double chunks = double(N) * (std::ceil(steps_hint / gs::kChunk) + 1.0) + 1.0;
@@ -313,13 +335,15 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
     if (reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return fail(GS_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     pb.queue = static_cast<unsigned int*>(workspace);
   }
+  const long long row = start_row(system, opt->precision);
   if (opt->record_tape) {
-    rc = set_tape(pb, d, opt, N, K, workspace, workspace_bytes);
+    rc = set_tape(pb, d, opt, N, K, workspace, workspace_bytes, row);
     if (rc) return rc;
     pb.record = 1;
   }
-  rc = set_order(pb, opt, N, workspace, workspace_bytes);
+  rc = set_order(pb, opt, N, workspace, workspace_bytes, row);
   if (rc) return rc;
+  if (need_ws) set_start(pb, kernel, N, workspace, workspace_bytes, row);
   if (need_ws) {
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -345,9 +369,10 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   gs::Problem pb = make_problem(N, y0, params, t0, t1, rtol, atol, K, saveat, opt);
   pb.y_out = y_out; pb.status = status; pb.n_acc = n_accept; pb.n_rej = n_reject;
-  rc = set_tape(pb, d, opt, N, K, workspace, workspace_bytes);
+  const long long row = start_row(system, opt->precision);
+  rc = set_tape(pb, d, opt, N, K, workspace, workspace_bytes, row);
   if (rc) return rc;
-  rc = set_order(pb, opt, N, workspace, workspace_bytes);  // of the forward re-solve
+  rc = set_order(pb, opt, N, workspace, workspace_bytes, row);  // of the forward re-solve
   if (rc) return rc;
   pb.queue = static_cast<unsigned int*>(workspace);
   pb.dLdy = dLdy; pb.dLdy0 = dLdy0; pb.dLdp = dLdparams;
@@ -356,11 +381,13 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
   if (!opt->reuse_tape) {
     cudaError_t e = cudaMemsetAsync(workspace, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    set_start(pb, kernel, N, workspace, workspace_bytes, row);
     pb.record = 1;
     e = forward_of(system, opt->method)(pb, c);
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
   }
   pb.record = 0;
+  pb.start = nullptr;
   // the reverse pass takes its work-queue counter from header bytes [4, 8)
   pb.queue = reinterpret_cast<unsigned int*>(static_cast<unsigned char*>(workspace) + 4);
   if (kernel == GS_KERNEL_PERSISTENT) {
@@ -368,7 +395,7 @@ int gs_vjp(int32_t system, int64_t N, const double* y0, const double* params, co
     if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
   }
   if (opt->order != GS_ORDER_NATURAL) {  // longest-first order of the reverse pass, by the recorded step counts
-    const Layout L = layout(N);
+    const Layout L = layout(N, K, stride_of(opt), row);
     unsigned char* base = static_cast<unsigned char*>(workspace);
     int32_t* order = reinterpret_cast<int32_t*>(base + L.order);
     const cudaError_t e1 = gs::build_order((long long)N, nullptr, pb.tape.n_rec,
@@ -422,7 +449,7 @@ int jvp_on(int32_t system, int64_t N, const double* y0, const double* params, co
     pb.n_work = n_work;
     pb.n_work_dev = n_work_dev;  // at most n_work entries (checked by the writer of the list)
   } else {
-    rc = set_order(pb, opt, N, workspace, workspace_bytes);
+    rc = set_order(pb, opt, N, workspace, workspace_bytes, start_row(system, opt->precision));
     if (rc) return rc;
   }
   const int group = opt->method == GS_VERN7 ? 1 : 4;

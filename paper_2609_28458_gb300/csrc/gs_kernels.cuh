@@ -66,8 +66,28 @@ __global__ void __launch_bounds__(128) k_plain(const Problem pb) {
   tr.finish(pb);
 }
 
-template <template <class> class SysT, class Tab, int PM, int MT = 0>
+// Prepared starts (Problem::start): init() for every trajectory of the launch, one thread each, rows
+// written for the persistent kernel; trajectories that init() already finishes (empty or non-finite
+// input) are finished here. Run as a plain kernel, a trajectory start no longer holds up the other
+// lanes of a persistent warp, and the persistent kernel's code loses init() and the starting-step
+// evaluation.
+template <template <class> class SysT, class Tab, int PM>
+__global__ void __launch_bounds__(128) k_start(const Problem pb) {
+  const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n_work;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const long long n = pb.work ? (long long)pb.work[i] : (long long)i;
+    Traj<SysT, Tab, PM> tr;
+    tr.init(pb, n);
+    if (tr.done) tr.finish(pb);
+    tr.save_start(pb);
+  }
+}
+
+// PRE: trajectories start from the rows k_start prepared (MT == 0, PM 0-2), else in place
+template <template <class> class SysT, class Tab, int PM, int MT = 0, bool PRE = false>
 __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_persist(const Problem pb) {
+  static_assert(!PRE || (MT == 0 && PM != 3), "prepared starts: modes 0-2 without sensitivities");
   Traj<SysT, Tab, PM, MT> tr;
   const unsigned long long n_work = pb.n_work_dev ? (unsigned long long)*pb.n_work_dev : (unsigned long long)pb.n_work;
   const unsigned lane = threadIdx.x & 31u;
@@ -85,9 +105,14 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM, MT>::fwd)) k_pe
       if (need) {
         const unsigned long long idx = (unsigned long long)base + unsigned(__popc(m & lt_mask));
         if (idx < n_work) {
-          tr.init(pb, pb.work ? (long long)pb.work[idx] : (long long)idx);
-          running = true;
-          if (tr.done) { tr.finish(pb); running = false; }
+          const long long traj = pb.work ? (long long)pb.work[idx] : (long long)idx;
+          if constexpr (PRE) {
+            running = tr.load_start(pb, traj);
+          } else {
+            tr.init(pb, traj);
+            running = true;
+            if (tr.done) { tr.finish(pb); running = false; }
+          }
         } else {
           exhausted = true;
         }
@@ -392,6 +417,13 @@ cudaError_t launch_forward_t(const Problem& pb0, const LaunchCfg& c) {
   if (eo != cudaSuccess) return eo;
   if (c.kernel == 2) {
     auto kern = k_persist<SysT, Tab, PM>;
+    if constexpr (PM != 3) {
+      if (pb.start) {  // the starts, in the launch's own (unordered) work list: coalesced input reads
+        const long long sgrid = (pb0.n_work + 127) / 128;
+        k_start<SysT, Tab, PM><<<unsigned(sgrid < 1 ? 1 : sgrid), 128, 0, c.stream>>>(pb0);
+        kern = k_persist<SysT, Tab, PM, 0, true>;
+      }
+    }
     long long grid = persistent_grid(kern, block, c.sm_limit);
     const long long per_block = (long long)block * pb.warp_lanes / 32;
     const long long need = (pb.n_work + per_block - 1) / per_block;
@@ -513,8 +545,20 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
   return cudaGetLastError();
 }
 
+// bytes of a prepared-start row (Problem::start) of a system in a precision mode (0: none, for
+// the df64 mode); the row does not depend on the method
+template <template <class> class SysT>
+long long start_row_t(int precision) {
+  switch (precision) {
+    case 0: return Traj<SysT, Tsit5, 0>::kStartBytes;
+    case 1: return Traj<SysT, Tsit5, 1>::kStartBytes;
+    case 2: return Traj<SysT, Tsit5, 2>::kStartBytes;
+    default: return 0;
+  }
+}
+
 // per-system, per-method entry points defined in gs_inst_<system>_<method>.cu, and the right-hand-side
-// evaluator of each system (in its Tsit5 unit)
+// evaluator and prepared-start row size of each system (in its Tsit5 unit)
 #define GS_DECLARE_METHOD(name, Tab)                                      \
   cudaError_t forward_##name##_##Tab(const Problem& pb, const LaunchCfg& c); \
   cudaError_t reverse_##name##_##Tab(const Problem& pb, const LaunchCfg& c); \
@@ -524,7 +568,8 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
   GS_DECLARE_METHOD(name, Dopri5)                                                                       \
   GS_DECLARE_METHOD(name, Vern7)                                                                        \
   cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p, \
-                         const double* w, double* f, double* gy, double* gp, cudaStream_t s);
+                         const double* w, double* f, double* gy, double* gp, cudaStream_t s);         \
+  long long start_row_##name(int precision);
 
 // The heaviest instantiations (precession) put the reverse kernels in a translation unit of their own
 // (GS_DEFINE_FORWARD_JVP + GS_DEFINE_REVERSE) so that the two halves compile in parallel.
@@ -546,6 +591,7 @@ cudaError_t launch_rhs(int precision, long long M, const double* t, const double
   cudaError_t rhs_##name(int precision, long long M, const double* t, const double* y, const double* p,  \
                          const double* w, double* f, double* gy, double* gp, cudaStream_t s) {           \
     return launch_rhs<SysT>(precision, M, t, y, p, w, f, gy, gp, s);                                    \
-  }
+  }                                                                                                      \
+  long long start_row_##name(int precision) { return start_row_t<SysT>(precision); }
 
 }  // namespace gs

@@ -118,6 +118,12 @@ struct Problem {
   const double* dLdy;
   double* dLdy0;
   double* dLdp;
+  // prepared starts (persistent forward solves without sensitivities, precision modes 0-2): k_start
+  // runs init() for every trajectory of the launch and leaves its state in row n of `start`
+  // (start_row bytes apart, 16-byte aligned); the persistent kernel then loads a row where it would
+  // otherwise start the trajectory itself. Null: the persistent kernel runs init() in place.
+  unsigned char* start;
+  long long start_row;
 };
 
 __device__ __forceinline__ double save_at(const Problem& pb, long long n, int k) {
@@ -1075,6 +1081,104 @@ struct Traj {
       err_prev = 1.0;
       lerr_prev = 0.0f;
     }
+  }
+
+  // ---- prepared start: the state init() leaves, as one row of 32-bit words. Layout: y (the FP32
+  // high parts, or FP64), the FP32 low parts (FP32 modes), k1, theta with its prepared constants,
+  // then PM 0, 1: h, rem_c, hmin_c, last_c (FP64); PM 2: h (FP64), th, tl, hf, t1h, t1l, svh, svl; then
+  // atolf, rtolf, status, kk, kend, flags (bit 0: sv_ok, bit 1: done at start). Not for PM 3 or
+  // with sensitivities (MT > 0): those start in place.
+  static constexpr int kRW = sizeof(R) / 4;
+  static constexpr int kSY = 0, kSLO = kSY + D * kRW, kSK1 = kSLO + (F32 ? D : 0), kSP = kSK1 + D * kRW;
+  static constexpr int kST = kSP + NPP * kRW;
+  static constexpr int kSTail = kST + (DF ? 9 : 8);
+  static constexpr int kStartWords = (kSTail + 6 + 3) / 4 * 4;
+  static constexpr int kStartBytes = 4 * kStartWords;
+
+  __device__ static void put_r(uint32_t* w, int o, float v) { w[o] = __float_as_uint(v); }
+  __device__ static void put_r(uint32_t* w, int o, double v) {
+    w[o] = uint32_t(__double2loint(v));
+    w[o + 1] = uint32_t(__double2hiint(v));
+  }
+  __device__ static void get_r(const uint32_t* w, int o, float& v) { v = __uint_as_float(w[o]); }
+  __device__ static void get_r(const uint32_t* w, int o, double& v) { v = __hiloint2double(int(w[o + 1]), int(w[o])); }
+
+  // the row of trajectory n after init() (done: init() finished it; the persistent kernel skips it)
+  __device__ void save_start(const Problem& pb) const {
+    static_assert(MT == 0 && !DD, "prepared starts are built for modes 0-2 without sensitivities");
+    uint32_t w[kStartWords];
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      put_r(w, kSY + i * kRW, y[i]);
+      put_r(w, kSK1 + i * kRW, k1[i]);
+      if constexpr (F32) w[kSLO + i] = __float_as_uint(ylo[i]);
+    }
+#pragma unroll
+    for (int q = 0; q < NPP; q++) put_r(w, kSP + q * kRW, p[q]);
+    put_r(w, kST, h);
+    if constexpr (DF) {
+      w[kST + 2] = __float_as_uint(th); w[kST + 3] = __float_as_uint(tl); w[kST + 4] = __float_as_uint(hf);
+      w[kST + 5] = __float_as_uint(t1h); w[kST + 6] = __float_as_uint(t1l);
+      w[kST + 7] = __float_as_uint(svh); w[kST + 8] = __float_as_uint(svl);
+    } else {
+      put_r(w, kST + 2, rem_c); put_r(w, kST + 4, hmin_c); put_r(w, kST + 6, BITS ? last_c : 0.0);
+    }
+    w[kSTail] = __float_as_uint(atolf);
+    w[kSTail + 1] = __float_as_uint(rtolf);
+    w[kSTail + 2] = uint32_t(status);
+    w[kSTail + 3] = uint32_t(kk);
+    w[kSTail + 4] = BITS ? uint32_t(kend) : 0u;
+    w[kSTail + 5] = (sv_ok ? 1u : 0u) | (done ? 2u : 0u);
+#pragma unroll
+    for (int q = kSTail + 6; q < kStartWords; q++) w[q] = 0u;
+    uint4* r4 = reinterpret_cast<uint4*>(pb.start + n * pb.start_row);
+#pragma unroll
+    for (int q = 0; q < kStartWords / 4; q++) r4[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+  }
+  // trajectory traj from its row: the state init() would leave. Returns false (nothing to do) for a
+  // trajectory that init() already finished.
+  __device__ bool load_start(const Problem& pb, long long traj) {
+    n = traj;
+    uint32_t w[kStartWords];
+    const uint4* r4 = reinterpret_cast<const uint4*>(pb.start + n * pb.start_row);
+#pragma unroll
+    for (int q = 0; q < kStartWords / 4; q++) {
+      const uint4 v = r4[q];
+      w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+    }
+    if (w[kSTail + 5] & 2u) return false;
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+      get_r(w, kSY + i * kRW, y[i]);
+      get_r(w, kSK1 + i * kRW, k1[i]);
+      if constexpr (F32) ylo[i] = __uint_as_float(w[kSLO + i]);
+    }
+#pragma unroll
+    for (int q = 0; q < NPP; q++) get_r(w, kSP + q * kRW, p[q]);
+    get_r(w, kST, h);
+    if constexpr (DF) {
+      th = __uint_as_float(w[kST + 2]); tl = __uint_as_float(w[kST + 3]); hf = __uint_as_float(w[kST + 4]);
+      t1h = __uint_as_float(w[kST + 5]); t1l = __uint_as_float(w[kST + 6]);
+      svh = __uint_as_float(w[kST + 7]); svl = __uint_as_float(w[kST + 8]);
+    } else {
+      get_r(w, kST + 2, rem_c); get_r(w, kST + 4, hmin_c); get_r(w, kST + 6, last_c);
+    }
+    atolf = __uint_as_float(w[kSTail]);
+    rtolf = __uint_as_float(w[kSTail + 1]);
+    status = int32_t(w[kSTail + 2]);
+    kk = int32_t(w[kSTail + 3]);
+    if constexpr (BITS) kend = int32_t(w[kSTail + 4]);
+    sv_ok = (w[kSTail + 5] & 1u) != 0u;
+    t0 = pb.t0[n];
+    t1 = pb.t1[n];
+    t = t0;
+    tc = 0.0;
+    if (kk < pb.K) sv = save_at(pb, n, kk);
+    nacc = 0; nrej = 0; chunk = -1;
+    done = false; failed = false; rec_ok = true;
+    err_prev = 1.0;
+    lerr_prev = 0.0f;
+    return true;
   }
 
   __device__ void finish(const Problem& pb) {
