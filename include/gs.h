@@ -360,14 +360,15 @@ int gs_alu_probe(int32_t kind, int64_t iters, int32_t blocks_per_sm, double* sin
 /* Device self-test of the bit-level FP64 helpers the kernels use instead of FP64-pipe instructions
  * (the paper has no counterpart; a GB300 cost, not a method step): FP64 -> FP32 rounding, FP32 -> FP64
  * widening, FP64 <= and ==, NaN and finiteness tests, sign operations (bit for bit on numbers; a NaN
- * gives a NaN), the order of non-negative numbers, and log2 to FP32 accuracy (within 2^-20 +
- * 2^-23 |log2 x|), each compared on the device with the instruction it replaces. n inputs per check
- * from SplitMix64 on the counters seed .. seed + 4n - 1: raw 64-bit patterns, numbers in and around
- * the FP32 range, rounding ties and their neighbours, and a fixed list of edge cases. counts: device
- * array of 2 x GS_SELFTEST_CHECKS entries, set by the call (stream-ordered on cuda_stream):
- * counts[c] the mismatches of check c, counts[GS_SELFTEST_CHECKS + c] the bit pattern of one
- * mismatching input (0 if none). */
-#define GS_SELFTEST_CHECKS 8
+ * gives a NaN), the order of non-negative numbers, log2 to FP32 accuracy (within 2^-20 +
+ * 2^-23 |log2 x|) and the step-size floor 16 eps max(|x|, |y|) of finite x, y (bit for bit where it
+ * is a normal number), each compared on the device with the instruction or FP64 expression it
+ * replaces. n inputs per check from SplitMix64 on the counters seed .. seed + 4n - 1: raw 64-bit
+ * patterns, numbers in and around the FP32 range, rounding ties and their neighbours, and a fixed
+ * list of edge cases. counts: device array of 2 x GS_SELFTEST_CHECKS entries, set by the call
+ * (stream-ordered on cuda_stream): counts[c] the mismatches of check c, counts[GS_SELFTEST_CHECKS + c]
+ * the bit pattern of one mismatching input (0 if none). */
+#define GS_SELFTEST_CHECKS 9
 int gs_selftest(int64_t n, uint64_t seed, unsigned long long* counts, void* cuda_stream);
 
 /* Message for the last non-zero return on this host thread ("" if none). */

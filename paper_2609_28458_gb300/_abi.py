@@ -27,7 +27,7 @@ EXPORTS = ("gs_default_options", "gs_dims", "gs_solve", "gs_vjp", "gs_jvp", "gs_
            "gs_profile_prepare", "gs_profile_workspace_bytes", "gs_profile_fit", "gs_rhs", "gs_last_error",
            "gs_version")
 NOALLOC_SCRATCH_BYTES = 64 << 20
-SELFTEST_CHECKS = 8  # GS_SELFTEST_CHECKS
+SELFTEST_CHECKS = 9  # GS_SELFTEST_CHECKS
 
 
 class GsOptions(ctypes.Structure):

@@ -342,7 +342,7 @@ def alu_peak(fp64=False, iters=None, blocks_per_sm=4, device=None, reps=3, packe
 
 
 SELFTEST_NAMES = ("narrow_f64", "widen_f32", "le_f64", "eq_f64", "nan_finite", "sign_ops", "le_nonneg_f64",
-                  "log2_f64_f32")
+                  "log2_f64_f32", "max_abs_2m48")
 
 
 def selftest(n=1 << 22, seed=0, device=None):

@@ -12,6 +12,10 @@
 // Each helper gives exactly the result of the operation it replaces for every input (conversions
 // as this library is built, with FP32 flush-to-zero: -ftz=true); gs_selftest() checks them on the
 // device against the hardware instructions.
+//
+// Sign masks work on the 32-bit high word: the compiler recognises a 64-bit "bits & 0x7fff...ffff"
+// of a double as fabs and issues it as an FP64 add with an absolute-value operand (measured: two
+// such masks per accepted step were two FP64 instructions per step).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -62,7 +66,8 @@ template <> __device__ __forceinline__ float to_r<float>(double x) { return narr
 // NaN pattern lies above that of +inf.
 __device__ __forceinline__ bool le_nonneg_f64(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
 __device__ __forceinline__ bool isnan_f64_bits(double x) {
-  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+  const uint32_t hi = uint32_t(__double2hiint(x)) & 0x7fffffffu;
+  return hi > 0x7ff00000u || (hi == 0x7ff00000u && __double2loint(x) != 0);
 }
 __device__ __forceinline__ bool isfinite_f64_bits(double x) {
   return (uint32_t(__double2hiint(x)) & 0x7ff00000u) != 0x7ff00000u;
@@ -78,8 +83,9 @@ __device__ __forceinline__ float log2_f64_f32(double x) {
 // A signed 64-bit key that orders non-NaN FP64 numbers as their values (-0 and +0 get the same key):
 // non-negative numbers keep their bit pattern, negative ones get minus their magnitude's pattern.
 __device__ __forceinline__ long long key_f64(double x) {
-  const long long b = __double_as_longlong(x);
-  return b < 0 ? -(b & 0x7fffffffffffffffLL) : b;
+  const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
+  const long long mag = (long long)(((unsigned long long)(hi & 0x7fffffffu) << 32) | lo);
+  return (hi & 0x80000000u) ? -mag : mag;
 }
 // x <= y and x == y as the FP64 comparisons give them; both false when either is NaN
 __device__ __forceinline__ bool le_f64_bits(double x, double y) {
@@ -88,13 +94,24 @@ __device__ __forceinline__ bool le_f64_bits(double x, double y) {
 __device__ __forceinline__ bool eq_f64_bits(double x, double y) {
   return !isnan_f64_bits(x) && key_f64(x) == key_f64(y);
 }
-// -x and |x| by the sign bit
+// -x and |x| by the sign bit of the high word
 __device__ __forceinline__ double neg_f64_bits(double x) {
-  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+  return __hiloint2double(int(uint32_t(__double2hiint(x)) ^ 0x80000000u), __double2loint(x));
 }
 __device__ __forceinline__ double abs_f64_bits(double x) {
-  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+  return __hiloint2double(int(uint32_t(__double2hiint(x)) & 0x7fffffffu), __double2loint(x));
 }
-__device__ __forceinline__ bool signbit_f64_bits(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool signbit_f64_bits(double x) { return __double2hiint(x) < 0; }
+// max(|a|, |b|) * 2^-48 (16 eps max(|a|, |b|) in FP64) of finite a, b, flushed to zero below the
+// normal range: the larger magnitude by its (high, low) words, then 48 off its exponent field
+__device__ __forceinline__ double max_abs_2m48_bits(double a, double b) {
+  const uint32_t ha = uint32_t(__double2hiint(a)) & 0x7fffffffu, la = uint32_t(__double2loint(a));
+  const uint32_t hb = uint32_t(__double2hiint(b)) & 0x7fffffffu, lb = uint32_t(__double2loint(b));
+  const bool a_big = ha > hb || (ha == hb && la >= lb);
+  const uint32_t hm = a_big ? ha : hb, lm = a_big ? la : lb;
+  const uint32_t e48 = 48u << 20;
+  const bool keep = hm > e48 || (hm == e48 && lm != 0u);
+  return keep ? __hiloint2double(int(hm - e48), int(lm)) : 0.0;
+}
 
 }  // namespace gs

@@ -117,6 +117,14 @@ __global__ void k_selftest(long long n, unsigned long long seed, unsigned long l
     // 6: order of non-negative numbers (the norm's accept test): x, y >= 0, not NaN
     const double ax = fabs(x), ay = fabs(y);
     if (!nan64(ax) && !nan64(ay) && gs::le_nonneg_f64(ax, ay) != (ax <= ay)) bad(counts, 6, xb);
+    // 8: 16 eps max(|x|, |y|) (the step-size floor) of finite x, y, where that product is normal
+    if (isfinite(x) && isfinite(y)) {
+      const double mx = fabs(x) > fabs(y) ? fabs(x) : fabs(y);
+      const double ref = 16.0 * 2.220446049250313e-16 * mx;
+      if (ref >= 2.2250738585072014e-308 &&
+          __double_as_longlong(gs::max_abs_2m48_bits(x, y)) != __double_as_longlong(ref))
+        bad(counts, 8, xb);
+    }
     // 7: log2 of a positive normal number to FP32 accuracy: the mantissa truncated to 24 bits
     // (2^-24 relative: 8.6e-8 in log2), the fast FP32 log2 on [1, 2) and the rounding of the FP32
     // sum (half an ulp of |log2 x| < 1024): within 2^-20 + 2^-23 |log2 x|

@@ -812,11 +812,7 @@ struct Traj {
       // the last-step threshold eight units in the last place below the remainder (rem (1 - 2^-50)
       // lies 4 to 8 units below it)
       rem_c = (t1 - t) + tc;
-      const long long at = __double_as_longlong(t) & 0x7fffffffffffffffLL;
-      const long long a1 = __double_as_longlong(t1) & 0x7fffffffffffffffLL;
-      const long long tm = at > a1 ? at : a1;
-      const long long e48 = 48LL << 52;
-      hmin_c = __longlong_as_double(tm > e48 ? tm - e48 : 0LL);
+      hmin_c = max_abs_2m48_bits(t, t1);
       const long long rb = __double_as_longlong(rem_c);
       last_c = __longlong_as_double(rb > 8LL ? rb - 8LL : 0LL);
     } else if constexpr (!DF) {
