@@ -192,3 +192,21 @@ def test_selftest_entry_checks_arguments_on_the_host(lib):
     assert len(api.SELFTEST_NAMES) == _abi.SELFTEST_CHECKS
     assert lib.gs_selftest(0, 0, None, None) == _abi.GS_ERR_INVALID
     assert lib.gs_selftest(16, 0, None, None) == _abi.GS_ERR_INVALID
+
+
+def test_workspace_holds_the_prepared_starts(lib):
+    """gs_workspace_bytes(for_vjp = 0) grows with N by the counters' 16 bytes plus a prepared-start row
+    per trajectory for the persistent forward (112 to 256 bytes by system and precision; none in
+    GS_DF64), and the part before the tape pool includes it."""
+    for name, sysid in (("mw", 1), ("precession", 2), ("isochrone", 0)):
+        for prec in ("fp64", "fp32", "fp32df"):
+            o = _abi.options(precision=prec)
+            a = lib.gs_workspace_bytes(sysid, 1 << 16, 1, ctypes.byref(o), 0, 0.0)
+            b = lib.gs_workspace_bytes(sysid, 2 << 16, 1, ctypes.byref(o), 0, 0.0)
+            per = (b - a) / float(1 << 16)
+            assert 16 + 112 <= per <= 16 + 256, (name, prec, per)
+            assert lib.gs_workspace_bytes(sysid, 1 << 16, 1, ctypes.byref(o), 1, 0.0) >= a
+    o = _abi.options(precision="df64")
+    a = lib.gs_workspace_bytes(0, 1 << 16, 1, ctypes.byref(o), 0, 0.0)
+    b = lib.gs_workspace_bytes(0, 2 << 16, 1, ctypes.byref(o), 0, 0.0)
+    assert (b - a) / float(1 << 16) == 16
