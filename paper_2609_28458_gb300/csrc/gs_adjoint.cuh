@@ -106,7 +106,7 @@ struct Adjoint {
     R y[D];          // the state at the step's start (FP32 modes: its high part; the low part is
                      // not recorded, the stages are recomputed from the high part as in the forward)
     float4 tf;       // PM 2 tail: th, tl, h, flag
-    double2 t0, t1;  // PM 0, 1 tail: (t, tc), (h, flag)
+    double tt, tc, hs;  // PM 0, 1 tail: t, tc, h (negative for the last step)
   };
   __device__ static void fetch(const unsigned char* s, Raw& r) {
     if constexpr (F32) {
@@ -148,9 +148,15 @@ struct Adjoint {
     if constexpr (DF) {
       r.tf = *reinterpret_cast<const float4*>(s + T::kTailOff);
     } else {
-      const double2* t = reinterpret_cast<const double2*>(s + T::kTailOff);
-      r.t0 = t[0];
-      r.t1 = t[1];
+      if constexpr (T::kTailOff % 16 == 0) {
+        const double2 a = *reinterpret_cast<const double2*>(s + T::kTailOff);
+        r.tt = a.x; r.tc = a.y;
+        r.hs = *reinterpret_cast<const double*>(s + T::kTailOff + 16);
+      } else {
+        r.tt = *reinterpret_cast<const double*>(s + T::kTailOff);
+        const double2 a = *reinterpret_cast<const double2*>(s + T::kTailOff + 8);
+        r.tc = a.x; r.hs = a.y;
+      }
     }
   }
   __device__ static SlotView decode(const Raw& r) {
@@ -161,8 +167,9 @@ struct Adjoint {
       v.tc = 0.0;
       v.h = double(v.hf);
     } else {
-      v.t = r.t0.x; v.tc = r.t0.y; v.h = r.t1.x;
-      v.last = (__double_as_longlong(r.t1.y) << 1) != 0;  // the flag is 1.0 or 0.0: tested on its bits
+      v.t = r.tt; v.tc = r.tc;
+      v.last = signbit_f64_bits(r.hs);  // (h > 0: the sign marks the last step)
+      v.h = abs_f64_bits(r.hs);
     }
     return v;
   }

@@ -48,11 +48,13 @@ int order_of(int32_t method) { return method == GS_VERN7 ? 7 : 5; }
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // tape slot (checkpoint stride 1): the state at the step's start (FP64, df64 pairs, or its FP32 high
-// part), padded to 16 bytes, then the times: t, tc, h, flag as FP64 (32 bytes), or th, tl, h, flag as
-// FP32 (16 bytes, PM 2 and 3)
+// part), then the times: t, tc, h as FP64 from the next 8-byte boundary (24 bytes; h negative for
+// the last step), or th, tl, h, flag as FP32 from the next 16-byte boundary (16 bytes, PM 2 and 3);
+// padded to 16 bytes
 long long slot_bytes(int32_t d, int32_t prec) {
   const long long state = (prec == GS_FP64 || prec == GS_DF64 ? 8LL : 4LL) * d;
-  return (state + 15) / 16 * 16 + (prec == GS_FP32_DF || prec == GS_DF64 ? 16 : 32);
+  if (prec == GS_FP32_DF || prec == GS_DF64) return (state + 15) / 16 * 16 + 16;  // FP32 tail th, tl, h, flag
+  return ((state + 7) / 8 * 8 + 24 + 15) / 16 * 16;  // FP64 tail t, tc, signed h
 }
 // checkpoint stride S > 1 (not PM 3): kChunk step lengths (FP64, FP32 in PM 2), then kChunk / S
 // checkpoints: state and first stage (FP64: 16 d bytes; FP32 modes: high part, low part and first

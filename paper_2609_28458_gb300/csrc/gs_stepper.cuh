@@ -222,15 +222,16 @@ struct Traj {
   static constexpr int NPP = PrepCount<Sys>::value > 0 ? PrepCount<Sys>::value : 1;  // theta + prepared constants
   static constexpr int DL = F32 ? D : 1;
   // slot layout: y[D] as FP64 (PM 0), its FP32 high part (PM 1, 2; the reverse pass recomputes
-  // the stages from the high part alone, as the forward attempt does) or its df64 pairs (PM 3),
-  // padded to a multiple of 16 bytes, then the tail: PM 0, 1: t, tc, h, flag (FP64, 32 bytes);
-  // PM 2, 3: th, tl, h, flag (FP32, 16 bytes). Chunk headers and slots are multiples of 16 bytes, so every slot, state and tail is
-  // 16-byte aligned for the vector loads and stores below.
+  // the stages from the high part alone, as the forward attempt does) or its df64 pairs (PM 3), then
+  // the tail: PM 0, 1: t, tc and the step length h (FP64, 24 bytes from the next 8-byte boundary;
+  // the last, clipped step of a trajectory with a negative sign); PM 2, 3: th, tl, h, flag (FP32,
+  // 16 bytes from the next 16-byte boundary). Slots are padded to 16 bytes and chunk headers are 16
+  // bytes, so every slot starts 16-byte aligned for the 16-byte stores and loads below.
   static constexpr int kStateBytes = (F32 ? 4 : 8) * D;
-  static constexpr int kTailOff = (kStateBytes + 15) / 16 * 16;
-  static constexpr int kSlotBytes = kTailOff + (DF ? 16 : 32);
-  static_assert(kTailOff % 16 == 0 && kSlotBytes % 16 == 0 && kChunkHeader % 16 == 0,
-                "tape slots must stay 16-byte aligned");
+  static constexpr int kTailOff = DF ? (kStateBytes + 15) / 16 * 16 : (kStateBytes + 7) / 8 * 8;
+  static constexpr int kSlotBytes = DF ? kTailOff + 16 : (kTailOff + 24 + 15) / 16 * 16;
+  static_assert(kTailOff % (DF ? 16 : 8) == 0 && kSlotBytes % 16 == 0 && kChunkHeader % 16 == 0,
+                "tape slots must stay aligned");
   static constexpr int kSlotWords = kSlotBytes / 4;
   static_assert(kStateBytes <= kTailOff, "state part of a slot overlaps its tail");
   // checkpoint stride S > 1: chunk = header, kChunk step lengths (FP64, or FP32 in PM 2), then
@@ -627,12 +628,15 @@ struct Traj {
       w[T0 + 2] = __float_as_uint(val(hstep));
       w[T0 + 3] = __float_as_uint(last ? 1.0f : 0.0f);
     } else {
-      const double tv[4] = {t, tc, h, last ? 1.0 : 0.0};
+      const double tv[3] = {t, tc, h};
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
+      for (int q = 0; q < 3; q++) {
         w[T0 + 2 * q] = uint32_t(__double2loint(tv[q]));
         w[T0 + 2 * q + 1] = uint32_t(__double2hiint(tv[q]));
       }
+      if (last) w[T0 + 5] |= 0x80000000u;  // the sign of h marks the last step
+#pragma unroll
+      for (int i = T0 + 6; i < kSlotWords; i++) w[i] = 0u;
     }
   }
   // A slot is written as kSlotBytes / 16 stores of 16 bytes, assembled in registers (state, zero

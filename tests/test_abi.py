@@ -74,14 +74,19 @@ def test_workspace_sizes(lib):
     big = lib.gs_workspace_bytes(1, 1000, 1, ctypes.byref(o), 1, 500.0)
     assert small >= 256 and big > small
     # a tape chunk holds 32 slots behind a 16-byte header; a slot is the state (8 d bytes in FP64,
-    # 4 d for the FP32 high part) rounded up to 16, then 32 bytes of times (16 in the FP32-pair mode)
-    assert (big - small) == (1000 * (16 + 1) + 1) * (16 + 32 * (48 + 32))
-    for prec, word, tail in (("fp64", 8, 32), ("fp32", 4, 32), ("fp32df", 4, 16)):
+    # 4 d for the FP32 high part), then the times: t, tc and the signed h as FP64 from the next
+    # 8-byte boundary (24 bytes), or th, tl, h, flag as FP32 from the next 16-byte boundary (16 bytes,
+    # FP32-pair mode); padded to 16 bytes
+    assert (big - small) == (1000 * (16 + 1) + 1) * (16 + 32 * 80)
+    for prec, word, fp32_tail in (("fp64", 8, False), ("fp32", 4, False), ("fp32df", 4, True)):
         o = _abi.options(precision=prec)
         for sysid, d in ((1, 6), (2, 9), (3, 3)):
             a = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 0, 0.0)
             b = lib.gs_workspace_bytes(sysid, 1000, 1, ctypes.byref(o), 1, 500.0)
-            slot = (word * d + 15) // 16 * 16 + tail
+            if fp32_tail:
+                slot = (word * d + 15) // 16 * 16 + 16
+            else:
+                slot = ((word * d + 7) // 8 * 8 + 24 + 15) // 16 * 16
             assert slot % 16 == 0 and (b - a) == (1000 * (16 + 1) + 1) * (16 + 32 * slot)
             # the binding's exact sizing uses the same chunk size
             na = torch.full((1000,), 500, dtype=torch.int32)
