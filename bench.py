@@ -339,8 +339,14 @@ def run_gpu(args):
     gsbuild.build()
     ctx = Ctx(dev)
 
-    # each rank integrates its own shard of the ensemble (weak scaling: N orbits per GPU)
-    e = W.mw(n=args.n, seed=1000 + rank, t1=T1_MYR, rtol=RTOL_GRAD)
+    # each rank integrates its own contiguous shard of a world x N-member ensemble (weak scaling: N
+    # orbits per GPU; the ensemble is defined block by block, block r seeded 1000 + r, so a rank draws
+    # only its own members)
+    from paper_2609_28458_gb300 import sharding
+
+    sh_start, sh_stop = sharding.shard_bounds(world * args.n, world, rank)
+    assert sh_stop - sh_start == args.n
+    e = W.mw(n=args.n, seed=1000 + sh_start // args.n, t1=T1_MYR, rtol=RTOL_GRAD)
     N = e.n
     y0 = torch.as_tensor(e.y0, device=dev)
     pr = torch.as_tensor(e.params, device=dev)
@@ -612,7 +618,8 @@ def run_gpu(args):
                        "kernel": "persistent forward (tape) + persistent reverse", "ckpt_stride": head_stride,
                        "rtol": RTOL_GRAD, "atol": RTOL_GRAD, "t1_myr": T1_MYR,
                        "budgets": {"orbit_p99": BUDGET, "sensitivity_p99": GRAD_BUDGET},
-                       "parallelism": "replicas (independent shards)" if world > 1 else "single GPU",
+                       "parallelism": ("replicas: rank %d of %d integrates members [%d, %d) of %d" %
+                                       (rank, world, sh_start, sh_stop, world * N)) if world > 1 else "single GPU",
                        "l2": "L2 flushed (256 MB write) before every timed step; tape %.0f GB per step" % tape_gb},
             "fwd_solves_per_s": world * N / (fwd_ms / 1e3),
             "fwd": {"rtol": RTOL_FWD_F32, "ms": fwd_ms, "accuracy": acc_fwd,
