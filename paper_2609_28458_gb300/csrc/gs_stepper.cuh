@@ -1065,10 +1065,7 @@ struct Traj {
       } else {
         next_time();
         time_cache();
-        if constexpr (F32) {
-          h = h * widen_f32(factor_f(pb, lerr));
-          lerr_prev = lerr > -13.287712f ? lerr : -13.287712f;
-        } else {
+        if constexpr (!F32) {  // (PM 1: the new h after both branches, below)
           h = h * factor_d(pb, err);
           err_prev = err > 1e-4 ? err : 1e-4;
         }
@@ -1076,10 +1073,21 @@ struct Traj {
     } else {
       nrej += 1;
       if constexpr (DF) hf = hf * (bad ? pb.falpha_min : factor_f(pb, lerr));
-      else if constexpr (F32) h = h * (bad ? pb.alpha_min : widen_f32(factor_f(pb, lerr)));
-      else h = h * (bad ? pb.alpha_min : factor_d(pb, err));
+      else if constexpr (!F32) h = h * (bad ? pb.alpha_min : factor_d(pb, err));
       err_prev = 1.0;
-      lerr_prev = 0.0f;
+      if constexpr (DF) lerr_prev = 0.0f;
+    }
+    if constexpr (F32 && !DF) {
+      // PM 1: the step-size update of both branches (an accepted step other than the last, and a
+      // rejected one) as one FP64 multiply after them, so that a warp whose lanes went both ways
+      // issues it once (the factor picked by an integer select of the two FP64 bit patterns). The
+      // factor takes the previous step's log2 ||e||, replaced only after it.
+      if (!done) {
+        const long long fb = bad ? __double_as_longlong(pb.alpha_min)
+                                 : __double_as_longlong(widen_f32(factor_f(pb, lerr)));
+        h = h * __longlong_as_double(fb);
+      }
+      lerr_prev = accept ? (lerr > -13.287712f ? lerr : -13.287712f) : 0.0f;
     }
   }
 
