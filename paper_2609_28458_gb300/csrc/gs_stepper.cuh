@@ -252,8 +252,9 @@ struct Traj {
   T k1[D];    // f(t, y): the first stage of the next attempt
   T p[NPP];
   double t, tc, h, t0, t1, err_prev, sv;  // PM 0, 1 (t0, t1 in all modes)
-  double rem_c, hmin_c;  // PM 0, 1: (t1 - t) + tc and 16 eps max(|t|, |t1|), updated when t is
-  double last_c;         // PM 1: the step length from which the step is the last (rem_c, 8 ulp less)
+  double rem_c, hmin_c;  // PM 0: (t1 - t) + tc and 16 eps max(|t|, |t1|), updated when t is
+  float remf;            // PM 1: an FP32 lower bound of the exact remainder t1 - t0 - (sum of the steps)
+  float marg;            // PM 1: an FP32 upper bound of 2^-47 max(|t0|, |t1|), at least 2^-100
   int32_t kend;          // PM 1: outputs kend.. are all at t1 (or unused): none is due before the last step
   float th, tl, hf, t1h, t1l, svh, svl;   // PM 2, 3
   float atolf, rtolf, lerr_prev;          // PM 1, 2, 3
@@ -513,6 +514,10 @@ struct Traj {
     if constexpr (BITS) {
       atolf = narrow_f64(pb.atol);
       rtolf = narrow_f64(pb.rtol);
+      // the bounds of the step-length test's fast path (attempt()); 2^-48 max(|t0|, |t1|) is 0
+      // below the normal range, and rounding to FP32 costs at most 2^-24 of it
+      marg = fmaxf(__fmul_ru(narrow_f64(max_abs_2m48_bits(t0, t1)), 2.0f + 0x1p-19f), 0x1p-100f);
+      remf = __fmaf_rd(narrow_f64(rem_c), 1.0f - 0x1p-20f, -marg);
       // the caller's first step (h0 > 0) at most the interval, else the starting-step heuristic;
       // rem_c = t1 - t0 > 0 here
       const long long hb = __double_as_longlong(pb.h0);
@@ -807,28 +812,15 @@ struct Traj {
       if constexpr (Tab::FSAL) k1[i] = k[S - 1][i];
     }
   }
-  // the quantities of the step-length tests that change only with the time (PM 0, 1): the remaining
-  // interval and the step-size floor of the underflow test
+  // the quantities of the step-length tests that change only with the time (PM 0): the remaining
+  // interval and the step-size floor of the underflow test. PM 1 forms them in attempt(), only when
+  // its FP32 bound does not settle the tests.
   __device__ __forceinline__ void time_cache() {
-    if constexpr (F32 && !DF) {
-      // PM 1: the same quantities with integer instructions wherever the FP64 pipe is not needed:
-      // |t|, |t1| and their maximum on the bit patterns; 16 eps tm = tm 2^-48 by the exponent field;
-      // the last-step threshold eight units in the last place below the remainder (rem (1 - 2^-50)
-      // lies 4 to 8 units below it)
-      rem_c = (t1 - t) + tc;
-      hmin_c = max_abs_2m48_bits(t, t1);
-      const long long rb = __double_as_longlong(rem_c);
-      last_c = __longlong_as_double(rb > 8LL ? rb - 8LL : 0LL);
-    } else if constexpr (!DF) {
+    if constexpr (!F32 && !DF) {
       rem_c = (t1 - t) + tc;
       const double tm = fabs(t) > fabs(t1) ? fabs(t) : fabs(t1);
       hmin_c = 16.0 * DBL_EPSILON * tm;
     }
-  }
-  // PM 1: (sv - t) + tc of the pending output; for an output at t1 it is the remainder itself
-  __device__ __forceinline__ double pending_dk() const {
-    if (__double_as_longlong(sv) == __double_as_longlong(t1)) return rem_c;
-    return (sv - t) + tc;
   }
   // the time after an accepted step that is not the last (Kahan summation, or the error-free
   // advance of the FP32 time pair), then the next first stage of pairs without FSAL
@@ -890,19 +882,33 @@ struct Traj {
       if constexpr (DD)
         if (last) hr = (R(t1h) + R(t1l)) - (R(th) + R(tl));
     } else if constexpr (F32) {
-      // PM 1: the same tests against the cached thresholds, compared as bit patterns (the values
-      // are non-negative, NaN apart), so that they take no slot of the FP64 pipe
-      if (__double_as_longlong(rem_c) <= 0LL) { close_interval(pb); return; }
-      if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
-      if (isnan_f64_bits(h)) { fail(ST_H_UNDERFLOW | ST_NONFINITE); return; }
-      if (le_nonneg_f64(last_c, h)) {
-        h = rem_c;
-        last = true;
-      } else if (!le_nonneg_f64(hmin_c, h)) {
-        fail(ST_H_UNDERFLOW);
-        return;
-      }
+      // PM 1: the same tests with the FP64 values compared as bit patterns (non-negative, NaN
+      // apart), the last-step threshold eight units in the last place below the remainder (where
+      // rem (1 - 2^-50) lies, 4 to 8 units below it) and 16 eps max(|t|, |t1|) formed by the exponent
+      // field. The remainder itself, two FP64 additions, is formed only where the FP32 bound remf
+      // does not settle the tests: with remf <= t1 - t0 - (sum of the steps) and h <= hr (1 + 2^-24),
+      // hr >= marg and hr (1 + 2^-10) + marg < remf give rem > 0, h < rem - 8 ulp and h above the
+      // floor, since the Kahan sum and the remainder's two roundings err by less than 2^-51 max(|t0|,
+      // |t1|) + 2^-52 rem. The decisions, and h, are those of the FP64 tests in every case.
       hr = cvt(h);
+      if (hr >= marg && __fmaf_ru(hr, 1.0f + 0x1p-10f, marg) < remf) {
+        if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+      } else {
+        const double rem = (t1 - t) + tc;
+        const long long rb = __double_as_longlong(rem);
+        if (rb <= 0LL) { close_interval(pb); return; }
+        if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
+        if (isnan_f64_bits(h)) { fail(ST_H_UNDERFLOW | ST_NONFINITE); return; }
+        if (le_nonneg_f64(__longlong_as_double(rb > 8LL ? rb - 8LL : 0LL), h)) {
+          h = rem;
+          hr = cvt(h);
+          last = true;
+        } else if (!le_nonneg_f64(max_abs_2m48_bits(t, t1), h)) {
+          fail(ST_H_UNDERFLOW);
+          return;
+        }
+        remf = __fmaf_rd(narrow_f64(rem), 1.0f - 0x1p-20f, -marg);  // below rem by more than its error
+      }
     } else {
       if (rem_c <= 0.0) { close_interval(pb); return; }
       if (nacc + nrej >= pb.max_steps) { fail(ST_MAX_STEPS); return; }
@@ -1011,9 +1017,14 @@ struct Traj {
           at_end = last && svh == t1h && svl == t1l;
           inside = last || ((svh - th) + (svl - tl)) <= hf;
         } else if constexpr (F32) {  // PM 1: h > 0, so the bit patterns order as the values
-          at_end = last && __double_as_longlong(sv) == __double_as_longlong(t1);
-          dk = pending_dk();
-          inside = last || __double_as_longlong(dk) <= __double_as_longlong(h);
+          const bool at_t1 = __double_as_longlong(sv) == __double_as_longlong(t1);
+          at_end = last && at_t1;
+          if (at_t1) {
+            inside = last;  // an output at t1 falls in the last step only
+          } else {
+            dk = (sv - t) + tc;
+            inside = last || __double_as_longlong(dk) <= __double_as_longlong(h);
+          }
         } else {
           at_end = last && sv == t1;
           inside = last || ((sv - t) + tc) <= h;
@@ -1065,6 +1076,9 @@ struct Traj {
       } else {
         next_time();
         time_cache();
+        // PM 1: the bound moves down by at least the step (hr (1 + 2^-22) >= h; marg covers an h
+        // below the FP32 normal range), rounded down
+        if constexpr (BITS) remf = __fmaf_rd(-fmaxf(hr, marg), 1.0f + 0x1p-22f, remf);
         if constexpr (!F32) {  // (PM 1: the new h after both branches, below)
           h = h * factor_d(pb, err);
           err_prev = err > 1e-4 ? err : 1e-4;
@@ -1093,7 +1107,8 @@ struct Traj {
 
   // ---- prepared start: the state init() leaves, as one row of 32-bit words. Layout: y (the FP32
   // high parts, or FP64), the FP32 low parts (FP32 modes), k1, theta with its prepared constants,
-  // then PM 0, 1: h, rem_c, hmin_c, last_c (FP64); PM 2: h (FP64), th, tl, hf, t1h, t1l, svh, svl; then
+  // then PM 0: h, rem_c, hmin_c (FP64), 0; PM 1: h (FP64), remf, marg, 0 (4 words); PM 2: h (FP64),
+  // th, tl, hf, t1h, t1l, svh, svl; then
   // atolf, rtolf, status, kk, kend, flags (bit 0: sv_ok, bit 1: done at start). Not for PM 3 or
   // with sensitivities (MT > 0): those start in place.
   static constexpr int kRW = sizeof(R) / 4;
@@ -1129,7 +1144,13 @@ struct Traj {
       w[kST + 5] = __float_as_uint(t1h); w[kST + 6] = __float_as_uint(t1l);
       w[kST + 7] = __float_as_uint(svh); w[kST + 8] = __float_as_uint(svl);
     } else {
-      put_r(w, kST + 2, rem_c); put_r(w, kST + 4, hmin_c); put_r(w, kST + 6, BITS ? last_c : 0.0);
+      if constexpr (BITS) {
+        w[kST + 2] = __float_as_uint(remf); w[kST + 3] = __float_as_uint(marg);
+#pragma unroll
+        for (int q = 4; q < 8; q++) w[kST + q] = 0u;
+      } else {
+        put_r(w, kST + 2, rem_c); put_r(w, kST + 4, hmin_c); put_r(w, kST + 6, 0.0);
+      }
     }
     w[kSTail] = __float_as_uint(atolf);
     w[kSTail + 1] = __float_as_uint(rtolf);
@@ -1169,7 +1190,11 @@ struct Traj {
       t1h = __uint_as_float(w[kST + 5]); t1l = __uint_as_float(w[kST + 6]);
       svh = __uint_as_float(w[kST + 7]); svl = __uint_as_float(w[kST + 8]);
     } else {
-      get_r(w, kST + 2, rem_c); get_r(w, kST + 4, hmin_c); get_r(w, kST + 6, last_c);
+      if constexpr (BITS) {
+        remf = __uint_as_float(w[kST + 2]); marg = __uint_as_float(w[kST + 3]);
+      } else {
+        get_r(w, kST + 2, rem_c); get_r(w, kST + 4, hmin_c);
+      }
     }
     atolf = __uint_as_float(w[kSTail]);
     rtolf = __uint_as_float(w[kSTail + 1]);
