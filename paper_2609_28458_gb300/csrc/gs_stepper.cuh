@@ -517,7 +517,7 @@ struct Traj {
       // the bounds of the step-length test's fast path (attempt()); 2^-48 max(|t0|, |t1|) is 0
       // below the normal range, and rounding to FP32 costs at most 2^-24 of it
       marg = fmaxf(__fmul_ru(narrow_f64(max_abs_2m48_bits(t0, t1)), 2.0f + 0x1p-19f), 0x1p-100f);
-      remf = __fmaf_rd(narrow_f64(rem_c), 1.0f - 0x1p-20f, -marg);
+      remf = remainder_bound(rem_c);
       // the caller's first step (h0 > 0) at most the interval, else the starting-step heuristic;
       // rem_c = t1 - t0 > 0 here
       const long long hb = __double_as_longlong(pb.h0);
@@ -812,6 +812,12 @@ struct Traj {
       if constexpr (Tab::FSAL) k1[i] = k[S - 1][i];
     }
   }
+  // PM 1: an FP32 number below the FP64 remainder rem by more than that remainder's error against
+  // the exact t1 - t0 - (sum of the steps): rem rounded to FP32 (at most FLT_MAX, which a remainder
+  // that rounds to infinity exceeds), less 2^-20 of itself and marg, rounded down
+  __device__ __forceinline__ float remainder_bound(double rem) const {
+    return __fmaf_rd(fminf(narrow_f64(rem), FLT_MAX), 1.0f - 0x1p-20f, -marg);
+  }
   // the quantities of the step-length tests that change only with the time (PM 0): the remaining
   // interval and the step-size floor of the underflow test. PM 1 forms them in attempt(), only when
   // its FP32 bound does not settle the tests.
@@ -907,7 +913,7 @@ struct Traj {
           fail(ST_H_UNDERFLOW);
           return;
         }
-        remf = __fmaf_rd(narrow_f64(rem), 1.0f - 0x1p-20f, -marg);  // below rem by more than its error
+        remf = remainder_bound(rem);
       }
     } else {
       if (rem_c <= 0.0) { close_interval(pb); return; }

@@ -17,6 +17,7 @@ import oracle as O
 from gpu_util import gpu_solve, rel_err
 from paper_2609_28458_gb300 import metrics as M
 from paper_2609_28458_gb300 import workloads as W
+from paper_2609_28458_gb300.workloads import Ensemble
 
 pytestmark = pytest.mark.gpu
 
@@ -160,6 +161,39 @@ def test_mw_meets_orbit_budget_at_searched_tolerance(kernel):
         assert np.all(g["status"] == 0)
         err = M.orbit_error(g["y"][:, -1], ref["y"][:, -1], rE, vE)
         assert M.accepted(err, 1e-4), (prec, M.p99(err), err.max())
+
+
+@pytest.mark.parametrize("t0, span", [(-1500.0, 750.0), (1e7, 750.0), (1e9, 1.0), (0.0, 1e-3)])
+def test_fp32_stages_time_arithmetic_on_shifted_intervals(t0, span):
+    """The precision split keeps the time as a Kahan-compensated FP64 sum and decides the last step
+    by an FP32 lower bound of the remaining interval wherever that bound settles it (the FP64 tests
+    elsewhere). Intervals that are negative, far from 0, short against their offset or tiny end on
+    t1 and give, at five outputs each, the oracle's FP64 same-algorithm solve within the orbit budget
+    (Eq. st-fwderr). The Milky-Way field is autonomous, so shifting the interval changes only the
+    rounding of the time: each member takes the step sequence of the same solve on [0, span] (the
+    last step's length apart) and reaches the same outputs."""
+    base = W.mw(n=512, seed=41, t1=span)
+
+    def on(t_start):
+        t0v = np.full(base.n, t_start)
+        t1v = t0v + span
+        sv = t0v[:, None] + span * np.linspace(0.0, 1.0, 5)[None, :]
+        sv[:, -1] = t1v
+        return Ensemble("mw", base.y0, base.params, t0v, t1v, sv, 1e-8, 1e-8, "tsit5")
+
+    e, e0 = on(t0), on(0.0)
+    ref = oracle_solve(e)
+    g = gpu_solve(e, precision="fp32", kernel="persistent")
+    g0 = gpu_solve(e0, precision="fp32", kernel="persistent")
+    assert np.all(g["status"] == 0) and np.all(ref["status"] == 0) and np.all(g0["status"] == 0)
+    rE, vE = M.orbit_scales("mw", e.y0, e.params)
+    for k in range(e.saveat.shape[1]):
+        err = M.orbit_error(g["y"][:, k], ref["y"][:, k], rE, vE)
+        assert M.p99(err) <= 1e-4, (k, M.p99(err))
+        assert M.p99(M.orbit_error(g["y"][:, k], g0["y"][:, k], rE, vE)) <= 1e-6, k
+    assert np.array_equal(g["y"][:, 0], e.y0)
+    d = g["n_accept"].astype(np.int64) - g0["n_accept"]
+    assert np.abs(d).max() <= 1 and np.mean(d == 0) >= 0.98, (np.abs(d).max(), np.mean(d == 0))
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp32df"])
