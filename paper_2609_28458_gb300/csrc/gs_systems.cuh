@@ -153,26 +153,30 @@ struct MilkyWay {
   }
   __device__ static void f_from(const R* y, const R* p, const Parts& s, R* out) {
     const R cd = p[0] * s.cd0, kb = p[1] * s.kb0, kh = p[2] * s.kh0;
+    const R sd = cd + kb + kh;  // the in-plane force is -(c_d + k_b + k_h) (x, y)
     out[0] = y[3]; out[1] = y[4]; out[2] = y[5];
-    out[3] = -(cd * y[0] + kb * y[0] + kh * y[0]);
-    out[4] = -(cd * y[1] + kb * y[1] + kh * y[1]);
+    out[3] = -sd * y[0];
+    out[4] = -sd * y[1];
     out[5] = -(cd * s.u2 + kb * y[2] + kh * s.vh2);
   }
   __device__ static void vjp_from(const R* y, const R* p, const R* w, const Parts& s, R* gy, R* gp) {
     const R x = y[0], yy = y[1], z = y[2];
     const R wv[3] = {w[3], w[4], w[5]};
     const R cd = p[0] * s.cd0, kb = p[1] * s.kb0, kh = p[2] * s.kh0;
-    const R uw = x * wv[0] + yy * wv[1] + s.u2 * wv[2];
-    const R xw = x * wv[0] + yy * wv[1] + z * wv[2];
-    const R vw = x * wv[0] + yy * wv[1] + s.vh2 * wv[2];
+    const R xy = x * wv[0] + yy * wv[1];
+    const R uw = xy + s.u2 * wv[2];
+    const R xw = xy + z * wv[2];
+    const R vw = xy + s.vh2 * wv[2];
     const R dfac = R(3) * cd * s.iD2;
     const R kbr = p[1] * s.kbr0;
     const R khm = p[2] * s.khm0;
+    // H w: the in-plane rows are (c_d + k_b + k_h) w_i plus x_i times one common term
+    const R sd = cd + kb + kh;
+    const R tp = kbr * xw + khm * vw - dfac * uw;
     R Hw[3];
-    Hw[0] = cd * wv[0] - dfac * uw * x + kb * wv[0] + kbr * xw * x + kh * wv[0] + khm * vw * x;
-    Hw[1] = cd * wv[1] - dfac * uw * yy + kb * wv[1] + kbr * xw * yy + kh * wv[1] + khm * vw * yy;
-    Hw[2] = cd * s.u3p * wv[2] - dfac * uw * s.u2 + kb * wv[2] + kbr * xw * z + kh * s.iq2 * wv[2] +
-            khm * vw * s.vh2;
+    Hw[0] = sd * wv[0] + tp * x;
+    Hw[1] = sd * wv[1] + tp * yy;
+    Hw[2] = (cd * s.u3p + kb + kh * s.iq2) * wv[2] + kbr * xw * z + khm * vw * s.vh2 - dfac * uw * s.u2;
     gy[0] = -Hw[0]; gy[1] = -Hw[1]; gy[2] = -Hw[2];
     gy[3] = w[0]; gy[4] = w[1]; gy[5] = w[2];
     gp[0] = -s.cd0 * uw;
