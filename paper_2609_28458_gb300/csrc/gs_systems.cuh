@@ -100,9 +100,13 @@ struct Isochrone {
 //      d(grad Phi_h)/dq = k_h' dm/dq v + k_h (0, 0, -2z/q^3), dm/dq = -z^2/(q^3 m).
 template <class R>
 struct MilkyWay {
-  static constexpr int D = 6, P = 4, PP = 6;  // p[4] = 1/q^2, p[5] = 1/q^3
+  static constexpr int D = 6, P = 4, PP = 6;  // prepared: p[0..2] = G M, p[4] = 1/q^2, p[5] = 1/q^3
   static constexpr bool AUTONOMOUS = true;
   __device__ static void prep(R* p) {
+    const R G = R(kGmw);
+    p[0] = G * p[0];
+    p[1] = G * p[1];
+    p[2] = G * p[2];
     const R iq = grcp(p[3]);
     p[4] = iq * iq;
     p[5] = p[4] * iq;
@@ -110,12 +114,12 @@ struct MilkyWay {
   // The position-dependent factors of the force and of its Jacobian. u = (x, y, u2) and
   // v = (x, y, vh2); FULL adds the Hessian and q-derivative factors the VJP needs.
   struct Parts {
-    R cd0, u2, iD2, kb0, kh0, vh2, iq2;  // c_d / M_d, A z / zeta, 1/D^2, k_b / M_b, k_h / M_h, z/q^2, 1/q^2
-    R u3p, kbr0, khm0, iq3;              // u3', k_b'/(r M_b), k_h'/(m M_h), 1/q^3
+    R cd0, u2, iD2, kb0, kh0, vh2, iq2;  // c_d / (G M_d), A z / zeta, 1/D^2, k_b / (G M_b), k_h / (G M_h), z/q^2, 1/q^2
+    R u3p, kbr0, khm0, iq3;              // u3', k_b'/(r G M_b), k_h'/(m G M_h), 1/q^3
   };
   template <bool FULL>
   __device__ static void parts(const R* y, const R* p, Parts& s) {
-    const R G = R(kGmw), a = R(3.0), b = R(0.28), c = R(1.0), rs = R(15.6);
+    const R a = R(3.0), b = R(0.28), c = R(1.0), rs = R(15.6);
     const R x = y[0], yy = y[1], z = y[2];
     const R R2 = x * x + yy * yy, z2 = z * z;
     const R zq = z2 + b * b;
@@ -128,13 +132,13 @@ struct MilkyWay {
     R iD = grsqrt(D2);
     iD = iD * (R(1.5) - R(0.5) * D2 * iD * iD);
     s.iD2 = iD * iD;
-    s.cd0 = G * s.iD2 * iD;
+    s.cd0 = s.iD2 * iD;
     s.u2 = A * z * izeta;
     const R r2 = R2 + z2;
     const R ir = grsqrt(r2);
     const R r = r2 * ir;
     const R irc = grcp(r + c);
-    s.kb0 = G * ir * irc * irc;
+    s.kb0 = ir * irc * irc;
     s.iq2 = p[4];
     const R m2 = R2 + z2 * s.iq2;
     const R im = grsqrt(m2);
@@ -142,12 +146,12 @@ struct MilkyWay {
     const R irsm = grcp(rs + m);
     const R psi = glog1p(m * R(1.0 / 15.6)) - m * irsm;
     const R im3 = im * im * im;
-    s.kh0 = G * psi * im3;
+    s.kh0 = psi * im3;
     s.vh2 = z * s.iq2;
     if constexpr (FULL) {
       s.u3p = izeta * izeta * (z2 + A * b * b * izeta);
-      s.kbr0 = -G * (R(3) * r + c) * (ir * ir * ir) * (irc * irc * irc);
-      s.khm0 = G * (im3 * irsm * irsm - R(3) * psi * im3 * (im * im));
+      s.kbr0 = -(R(3) * r + c) * (ir * ir * ir) * (irc * irc * irc);
+      s.khm0 = im3 * irsm * irsm - R(3) * psi * im3 * (im * im);
       s.iq3 = p[5];
     }
   }
@@ -179,9 +183,11 @@ struct MilkyWay {
     Hw[2] = (cd * s.u3p + kb + kh * s.iq2) * wv[2] + kbr * xw * z + khm * vw * s.vh2 - dfac * uw * s.u2;
     gy[0] = -Hw[0]; gy[1] = -Hw[1]; gy[2] = -Hw[2];
     gy[3] = w[0]; gy[4] = w[1]; gy[5] = w[2];
-    gp[0] = -s.cd0 * uw;
-    gp[1] = -s.kb0 * xw;
-    gp[2] = -s.kh0 * vw;
+    // (the masses' cotangents: the prepared p[0..2] are G times the parameters)
+    const R G = R(kGmw);
+    gp[0] = -G * s.cd0 * uw;
+    gp[1] = -G * s.kb0 * xw;
+    gp[2] = -G * s.kh0 * vw;
     // -(k_h' dm/dq (v.w) + k_h (-2 z/q^3) w_z), dm/dq = -z^2/(q^3 m)
     gp[3] = khm * z * z * s.iq3 * vw + R(2) * kh * z * s.iq3 * wv[2];
   }
