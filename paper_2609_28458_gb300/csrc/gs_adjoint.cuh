@@ -609,7 +609,7 @@ struct Adjoint {
 #pragma unroll
     for (int i = 0; i < D; i++) gy0[i] = to_f64(ybar[i]);
 #pragma unroll
-    for (int q = 0; q < NP; q++) pb.dLdp[n * NP + q] = pacc.get(q);
+    for (int q = 0; q < NP; q++) pb.dLdp[n * NP + q] = pacc.get(q) * VjpParamScale<Sys>::of(q);
     done = true;
   }
 };

@@ -261,7 +261,7 @@ __global__ void k_rhs(long long M, const double* t, const double* y, const doubl
     if (gy)
       for (int i = 0; i < D; i++) gy[n * D + i] = double(gyy[i]);
     if (gp)
-      for (int q = 0; q < NP; q++) gp[n * NP + q] = double(gpp[q]);
+      for (int q = 0; q < NP; q++) gp[n * NP + q] = double(gpp[q]) * VjpParamScale<Sys>::of(q);
   }
 }
 

@@ -171,26 +171,27 @@ struct MilkyWay {
     const R uw = xy + s.u2 * wv[2];
     const R xw = xy + z * wv[2];
     const R vw = xy + s.vh2 * wv[2];
-    const R dfac = R(3) * cd * s.iD2;
-    const R kbr = p[1] * s.kbr0;
-    const R khm = p[2] * s.khm0;
-    // H w: the in-plane rows are (c_d + k_b + k_h) w_i plus x_i times one common term
+    // H w = (c_d + k_b + k_h) w (with c_d u3' and k_h/q^2 in the z row) plus the rank-one parts
+    // k_b'/r (x.w) x + k_h'/m (v.w) v - 3 c_d/D^2 (u.w) u; the in-plane rows share x_i times one term
+    const R bx = p[1] * s.kbr0 * xw, hv = p[2] * s.khm0 * vw, du = R(3) * cd * s.iD2 * uw;
     const R sd = cd + kb + kh;
-    const R tp = kbr * xw + khm * vw - dfac * uw;
+    const R tp = bx + hv - du;
     R Hw[3];
     Hw[0] = sd * wv[0] + tp * x;
     Hw[1] = sd * wv[1] + tp * yy;
-    Hw[2] = (cd * s.u3p + kb + kh * s.iq2) * wv[2] + kbr * xw * z + khm * vw * s.vh2 - dfac * uw * s.u2;
+    Hw[2] = (cd * s.u3p + kb + kh * s.iq2) * wv[2] + bx * z + hv * s.vh2 - du * s.u2;
     gy[0] = -Hw[0]; gy[1] = -Hw[1]; gy[2] = -Hw[2];
     gy[3] = w[0]; gy[4] = w[1]; gy[5] = w[2];
-    // (the masses' cotangents: the prepared p[0..2] are G times the parameters)
-    const R G = R(kGmw);
-    gp[0] = -G * s.cd0 * uw;
-    gp[1] = -G * s.kb0 * xw;
-    gp[2] = -G * s.kh0 * vw;
+    // the masses' cotangents per unit of the prepared G M (vjp_param_scale: the caller multiplies
+    // by G once per trajectory)
+    gp[0] = -s.cd0 * uw;
+    gp[1] = -s.kb0 * xw;
+    gp[2] = -s.kh0 * vw;
     // -(k_h' dm/dq (v.w) + k_h (-2 z/q^3) w_z), dm/dq = -z^2/(q^3 m)
-    gp[3] = khm * z * z * s.iq3 * vw + R(2) * kh * z * s.iq3 * wv[2];
+    gp[3] = z * s.iq3 * (hv * z + R(2) * kh * wv[2]);
   }
+  // the factor from gp[q] as vjp gives it to the cotangent of parameter q: G for the masses
+  __device__ static double vjp_param_scale(int q) { return q < 3 ? kGmw : 1.0; }
   __device__ static void f(R, const R* y, const R* p, R* out) {
     Parts s;
     parts<false>(y, p, s);
@@ -572,5 +573,14 @@ __device__ __forceinline__ void prep_params(Rp* p) {
 // float4s per stage that a system's f_save leaves for its vjp_saved (0: the system has neither)
 template <class Sys, class = void> struct SaveQ { static constexpr int value = 0; };
 template <class Sys> struct SaveQ<Sys, std::void_t<decltype(Sys::kSaveQ)>> { static constexpr int value = Sys::kSaveQ; };
+// The factor that turns a system's parameter cotangent, as its vjp returns it, into the cotangent of
+// the parameter itself: 1, except where prep() rescales a parameter and vjp differentiates by the
+// prepared value (the Milky-Way masses, prepared as G M). Callers apply it once per trajectory.
+template <class Sys, class = void> struct VjpParamScale {
+  __device__ static double of(int) { return 1.0; }
+};
+template <class Sys> struct VjpParamScale<Sys, std::void_t<decltype(Sys::vjp_param_scale(0))>> {
+  __device__ static double of(int q) { return Sys::vjp_param_scale(q); }
+};
 
 }  // namespace gs
