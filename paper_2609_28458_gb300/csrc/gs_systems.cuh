@@ -145,13 +145,16 @@ struct MilkyWay {
     const R m = m2 * im;
     const R irsm = grcp(rs + m);
     const R psi = glog1p(m * R(1.0 / 15.6)) - m * irsm;
-    const R im3 = im * im * im;
+    const R im2 = im * im;
+    const R im3 = im2 * im;
     s.kh0 = psi * im3;
     s.vh2 = z * s.iq2;
     if constexpr (FULL) {
       s.u3p = izeta * izeta * (z2 + A * b * b * izeta);
-      s.kbr0 = -(R(3) * r + c) * (ir * ir * ir) * (irc * irc * irc);
-      s.khm0 = im3 * irsm * irsm - R(3) * psi * im3 * (im * im);
+      // k_b'/r = -(3r + c) / (r^3 (r + c)^3) and k_h'/m = (1/(r_s + m)^2 - 3 psi/m^2) / m^3, from the
+      // force factors above
+      s.kbr0 = -(R(3) * r + c) * s.kb0 * (ir * ir) * irc;
+      s.khm0 = im3 * (irsm * irsm - R(3) * psi * im2);
       s.iq3 = p[5];
     }
   }
