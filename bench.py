@@ -64,9 +64,17 @@ ORACLE_RTOL = 1e-13  # the converged reference (Appendix A: the paper's referenc
 #                          6 VJPs, and the cotangent algebra 2d (15 a_lj + 6 b_j) = 2130
 # Of the ~40 flops of error norm and controller, the precision split keeps 2d + 5 in FP64: the d
 # squares accumulated (2d), the compensated time (4) and the step-size update (1).
+# The FP32 modes take the stages of second-order systems (y = (x, v), f = (v, a(x))) in Nystrom form:
+# the stage positions from the coefficients (A^2)_jm (zero for m >= j - 1) and the row sums of A,
+# over the d/2 position components only, and the position error from ((b - bhat) A)_m. Counted the
+# same way, a forward attempt is (S - 1) f + d (nnz A^2 + S - 1) + d (nnz((b - bhat) A) + nnz(b - bhat))
+# + 40 = 468 + 6*(15+6) + 6*(6+7) + 40 = 712, and a reversed step recomputes its stages with
+# d (nnz A^2 among the 6 + 2*5) = 6*(10+10) instead of 2d (15 + 5): 2010.
 F_RHS_MW = 78
 F_ATT_FWD = 6 * F_RHS_MW + 2 * 6 * (21 + 7) + 40
 F_STEP_REV = 6 * F_RHS_MW + 2 * 6 * (15 + 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
+F_ATT_FWD_NY = 6 * F_RHS_MW + 6 * (15 + 6) + 6 * (6 + 7) + 40
+F_STEP_REV_NY = 6 * F_RHS_MW + 6 * (10 + 2 * 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
 F64_ATT_SPLIT = 2 * 6 + 5
 # Forward flops of the other workloads, the same count for any system and tableau: per attempt
 # (S - 1) f + 2d (nnz A + nnz(b - bhat)) + 40, plus 2d nnz b for the new state and one f per accepted
@@ -75,21 +83,38 @@ F64_ATT_SPLIT = 2 * 6 + 5
 # Nonzeros of the published tableaux (S, FSAL, nnz A, nnz b, nnz(b - bhat)):
 F_RHS = {"mw": 78, "precession": 172, "isochrone": 14, "loghalo": 30, "quintessence": 40}
 TABLEAU_NNZ = {"tsit5": (7, True, 21, 6, 7), "dopri5": (7, True, 20, 5, 6), "vern7": (10, False, 36, 7, 8)}
+# Nystrom form (FP32 modes, second-order systems, the 7-stage FSAL pairs): nnz A^2 over stages 2..S,
+# nnz A^2 over the first 6 stages, nnz((b - bhat) A)
+NYSTROM_NNZ = {"tsit5": (15, 10, 6), "dopri5": (14, 10, 5)}
+SECOND_ORDER = ("mw", "isochrone", "loghalo")
 
 
-def forward_flops(system, method, d, attempts, accepted):
+def nystrom(system, method, prec):
+    return prec in ("fp32", "fp32df") and system in SECOND_ORDER and method in NYSTROM_NNZ
+
+
+def forward_flops(system, method, d, attempts, accepted, prec="fp64"):
     S, fsal, n_a, n_b, n_e = TABLEAU_NNZ[method]
     f = F_RHS[system]
+    if nystrom(system, method, prec):
+        n_aa, _, n_ea = NYSTROM_NNZ[method]
+        return attempts * ((S - 1) * f + d * (n_aa + S - 1) + d * (n_ea + n_e) + 40)
     per_attempt = (S - 1) * f + 2 * d * (n_a + (0 if fsal else n_b) + n_e) + 40
     return attempts * per_attempt + (0 if fsal else accepted * f)
 
 
-def reverse_flops(system, method, d, accepted):
-    """Per accepted step: the stages recomputed (S - 1 f + 2d nnz A), S VJPs at 2.5 f, and the
-    cotangent algebra 2d (nnz A + nnz b)."""
+def reverse_flops(system, method, d, accepted, prec="fp64"):
+    """Per accepted step: the stages recomputed (S - 1 f + 2d nnz A; Nystrom form: d (nnz A^2 among
+    the first 6 stages + 2*5)), S VJPs at 2.5 f, and the cotangent algebra 2d (nnz A + nnz b)."""
     S, fsal, n_a, n_b, n_e = TABLEAU_NNZ[method]
     f = F_RHS[system]
-    return accepted * ((S - 1) * f + 2 * d * n_a + S * int(2.5 * f) + 2 * d * (n_a + n_b))
+    recompute = d * (NYSTROM_NNZ[method][1] + 10) if nystrom(system, method, prec) else 2 * d * n_a
+    return accepted * ((S - 1) * f + recompute + S * int(2.5 * f) + 2 * d * (n_a + n_b))
+
+
+def att_flops(prec):
+    """Flops of one Milky-Way Tsit5 forward attempt and one reversed step in precision prec."""
+    return (F_ATT_FWD_NY, F_STEP_REV_NY) if nystrom("mw", "tsit5", prec) else (F_ATT_FWD, F_STEP_REV)
 
 
 # DRAM bytes per accepted step of the headline's kernels (forward recording the tape, reverse), from
@@ -477,11 +502,11 @@ def run_gpu(args):
     # roofline of the dominant kernel of the headline step
     fk, rk = float(np.mean(t_fwd)), float(np.mean(t_rev))
     if rk >= fk:
-        dom, flops, dur = "k_reverse_persist (discrete adjoint, %s)" % HEAD_PREC, n_acc * F_STEP_REV, rk
+        dom, flops, dur = "k_reverse_persist (discrete adjoint, %s)" % HEAD_PREC, n_acc * att_flops(HEAD_PREC)[1], rk
         bps = REV_DRAM_BYTES_PER_STEP.get(HEAD_PREC)
         traffic = bps * n_acc if bps else None
     else:
-        dom, flops, dur = "k_persist (forward + tape record, %s)" % HEAD_PREC, n_att * F_ATT_FWD, fk
+        dom, flops, dur = "k_persist (forward + tape record, %s)" % HEAD_PREC, n_att * att_flops(HEAD_PREC)[0], fk
         bps = FWD_DRAM_BYTES_PER_STEP.get(HEAD_PREC)
         traffic = bps * n_acc if bps else None
     achieved = flops / (dur / 1e3) / 1e12
@@ -491,7 +516,7 @@ def run_gpu(args):
     if dom.startswith("k_persist"):
         # the precision split also keeps 2d + 5 FP64 flops per attempt: the kernel's attainable time is
         # the longer of its FP32 and FP64 work at their measured peaks
-        t32 = n_att * F_ATT_FWD / (ctx.peak32 * 1e12)
+        t32 = n_att * att_flops(HEAD_PREC)[0] / (ctx.peak32 * 1e12)
         t64 = n_att * F64_ATT_SPLIT / (ctx.peak64 * 1e12)
         roofline["split_attainable_ms"] = 1e3 * max(t32, t64)
         roofline["frac_of_split_roofline"] = 1e3 * max(t32, t64) / dur
@@ -539,11 +564,11 @@ def run_gpu(args):
     d2h = out_y0.numel() * 8 + out_p.numel() * 8
 
     kernels = [dict(kernel="k_persist (forward + tape record, %s)" % HEAD_PREC, ms=fk,
-                    **ctx.frac(n_att * F_ATT_FWD, fk, HEAD_PREC)),
+                    **ctx.frac(n_att * att_flops(HEAD_PREC)[0], fk, HEAD_PREC)),
                dict(kernel="k_reverse_persist (discrete adjoint, %s)" % HEAD_PREC, ms=rk,
-                    **ctx.frac(n_acc * F_STEP_REV, rk, HEAD_PREC)),
+                    **ctx.frac(n_acc * att_flops(HEAD_PREC)[1], rk, HEAD_PREC)),
                dict(kernel="k_persist (forward, %s, estimate order)" % HEAD_PREC, ms=fwd_ms,
-                    **ctx.frac(fwd_att * F_ATT_FWD, fwd_ms, HEAD_PREC))]
+                    **ctx.frac(fwd_att * att_flops(HEAD_PREC)[0], fwd_ms, HEAD_PREC))]
 
     # ---------------- FP64 anchors and the other variants, each at its own budget tolerance ----------------
     def arm(prec, kernel, rf, reps):
@@ -557,9 +582,9 @@ def run_gpu(args):
         f_ms, so = ctx.timed(fw, reps, 1)
         fa, fc = _counts(so)
         kf = dict(kernel="k_%s (forward, %s)" % ("plain" if kernel == "plain" else "persist", prec), ms=f_ms,
-                  **ctx.frac(fa * F_ATT_FWD, f_ms, prec))
+                  **ctx.frac(fa * att_flops(prec)[0], f_ms, prec))
         kg = dict(kernel="forward + tape and reverse, %s %s" % (kernel, prec), ms=g_ms,
-                  **ctx.frac(ga * F_ATT_FWD + gc * F_STEP_REV, g_ms, prec))
+                  **ctx.frac(ga * att_flops(prec)[0] + gc * att_flops(prec)[1], g_ms, prec))
         row = {"precision": prec, "kernel": kernel, "reps": reps, "ckpt_stride": stride,
                "fwd_rtol": rf, "fwd_ms": f_ms, "fwd_solves_per_s": world * N / (f_ms / 1e3),
                "fwd_accuracy": acc_block(so["y"]), "fwd_frac_of_peak": kf["frac"],
@@ -685,7 +710,7 @@ def _solve_rows(ctx, system, e, rows, errfn, reps, grad_stride=None):
                "attempts_mean": att / e.n, "failed": int(((s["status"] & 7) != 0).sum().item())}
         row.update(errfn(s["y"]))
         if system in F_RHS and prec != "df64":
-            row["fwd_frac_of_peak"] = ctx.frac(forward_flops(system, meth, d, att, acc), f_ms, prec)["frac"]
+            row["fwd_frac_of_peak"] = ctx.frac(forward_flops(system, meth, d, att, acc, prec), f_ms, prec)["frac"]
             row["peak_kind"] = "FP64" if prec == "fp64" else "FP32"
         if grad:
             stride = row_stride or autotune.pick_stride(system, e.n, s["n_accept"], prec,
@@ -705,7 +730,7 @@ def _solve_rows(ctx, system, e, rows, errfn, reps, grad_stride=None):
             row.update(fwd_grad_ms=g_ms, fwd_grad_solves_per_s=e.n / (g_ms / 1e3), ckpt_stride=stride,
                        tape_gb=nb / 1e9)
             if system in F_RHS and prec != "df64":
-                fl = forward_flops(system, meth, d, att, acc) + reverse_flops(system, meth, d, acc)
+                fl = forward_flops(system, meth, d, att, acc, prec) + reverse_flops(system, meth, d, acc, prec)
                 row["fwd_grad_frac_of_peak"] = ctx.frac(fl, g_ms, prec)["frac"]
             del ws
         out.append(row)

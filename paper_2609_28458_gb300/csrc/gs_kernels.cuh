@@ -26,16 +26,16 @@ struct LaunchCfg {
 };
 
 // Resident 128-thread blocks per SM requested from the register allocator (__launch_bounds__), for
-// 7-stage pairs on states of at most 6 components: the FP32-pipe forward 4 (128 registers; measured on
-// the 3 Gyr Milky-Way ensemble with the explicit fused multiply-adds of the stage sums: forward 28.1 ms
-// against 30.7 ms at 5 blocks, where 96 registers spill; before those, 5 blocks had been 1-2% faster;
-// 6 blocks 42% slower), the FP64-control forward 4, the FP32 reverse 3 (<= 168; 2 blocks is 15%
-// slower, 4 blocks 5%), without spills. The FP64 forward of the 9-component
+// 7-stage pairs on states of at most 6 components: the FP32-pipe forward 5 (96 registers; measured on
+// the 3 Gyr Milky-Way ensemble: with the stages in Nystrom form, forward with tape 29.1 ms against
+// 33.4 ms at 4 blocks; in the general form 4 blocks had been faster, 28.1 against 30.7 ms forward
+// alone, and 6 blocks 42% slower), the FP64-control forward 4 (115 registers; 5 blocks: 35.5 against
+// 35.3 ms), the FP32 reverse 3 (<= 168; 2 blocks is 15% slower, 4 blocks 5%). The FP64 forward of the 9-component
 // precession state 4 blocks (16 warps per SM at 128 registers, against 8 at the compiler's 255: the
 // FP64 pipe gets more warps to overlap; 10^6 Verner 7 solves 243.9 -> 222.5 ms despite spilling, 3
 // blocks 229.9 ms). Other FP64 and Verner 7 kernels keep the compiler's choice.
 #ifndef GS_FWD_BLOCKS_FP32DF
-#define GS_FWD_BLOCKS_FP32DF 4
+#define GS_FWD_BLOCKS_FP32DF 5
 #endif
 #ifndef GS_FWD_BLOCKS_FP32
 #define GS_FWD_BLOCKS_FP32 4

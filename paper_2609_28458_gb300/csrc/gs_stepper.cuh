@@ -221,6 +221,11 @@ struct Traj {
   static constexpr int NPA = NP > 0 ? NP : 1;
   static constexpr int NPP = PrepCount<Sys>::value > 0 ? PrepCount<Sys>::value : 1;  // theta + prepared constants
   static constexpr int DL = F32 ? D : 1;
+  // FP32 modes on second-order systems with a 7-stage FSAL pair: the stages in Nystrom form
+  // (gs_tableaux.cuh, Nystrom): stage sums over the DH position components only
+  static constexpr bool RKN = F32 && MT == 0 && Tab::FSAL && Tab::S == 7 && SecondOrder<Sys>::value;
+  static constexpr int DH = D / 2;
+  using NY = Nystrom<Tab>;
   // slot layout: y[D] as FP64 (PM 0), its FP32 high part (PM 1, 2; the reverse pass recomputes
   // the stages from the high part alone, as the forward attempt does) or its df64 pairs (PM 3), then
   // the tail: PM 0, 1: t, tc and the step length h (FP64, 24 bytes from the next 8-byte boundary;
@@ -545,22 +550,35 @@ struct Traj {
   __device__ __forceinline__ void stages(double tt, double hh, T (*k)[D], T (*Y)[D], int nst, unsigned sl = 0,
                                          unsigned st = 0) const {
     const R hr = cvt(hh);
+    [[maybe_unused]] R hr2;
+    [[maybe_unused]] T hv[DH];
+    if constexpr (RKN) {
+      hr2 = hr * hr;
+#pragma unroll
+      for (int i = 0; i < DH; i++) hv[i] = hr * y[DH + i];
+    }
 #pragma unroll
     for (int i = 0; i < D; i++) { k[0][i] = k1[i]; if (Y) Y[0][i] = y[i]; }
 #pragma unroll
     for (int j = 1; j < S; j++) {
       if (j < nst) {
         T Yj[D];
+        if constexpr (RKN) {
+          nystrom_stage(j, hr2, hv, k, Yj);
+        } else {
 #pragma unroll
-        for (int i = 0; i < D; i++) {
-          T acc = T(R(0));
+          for (int i = 0; i < D; i++) {
+            T acc = T(R(0));
 #pragma unroll
-          for (int l = 0; l < j; l++)
-            if (Tab::a(j, l) != 0.0) acc = fmadd(R(Tab::a(j, l)), k[l][i], acc);
-          if constexpr (F32 || DD) Yj[i] = fmadd(hr, acc, y[i]);
-          else Yj[i] = fmadd(hh, acc, y[i]);
-          if (Y) Y[j][i] = Yj[i];
+            for (int l = 0; l < j; l++)
+              if (Tab::a(j, l) != 0.0) acc = fmadd(R(Tab::a(j, l)), k[l][i], acc);
+            if constexpr (F32 || DD) Yj[i] = fmadd(hr, acc, y[i]);
+            else Yj[i] = fmadd(hh, acc, y[i]);
+          }
         }
+        if (Y)
+#pragma unroll
+          for (int i = 0; i < D; i++) Y[j][i] = Yj[i];
         if constexpr (SAVE) {
           constexpr int Q = SaveQ<Sys>::value;
           if constexpr (DF) Sys::f_save(R(tt) + R(Tab::c(j)) * hr, Yj, p, k[j], sl + unsigned(j * Q) * st, st);
@@ -577,7 +595,35 @@ struct Traj {
   // Solution at tt + sig*hh inside the accepted step just taken (Eq. dense; Verner 7: shortened
   // step from the start of the step). k holds the step's stages.
   __device__ void dense_point(double tt, double hh, R sig, T (*k)[D], T* hi, T* lo) const {
-    if constexpr (Tab::DENSE_POLY) {
+    if constexpr (RKN) {
+      // Nystrom form: sum_j w_j V_j = (sum_j w_j) v + h sum_m (w A)_m a_m, from the accelerations
+      R w[S], wa[S];
+      Tab::dense(sig, w);
+      const R hr = R(hh);
+      R ws = R(0);
+#pragma unroll
+      for (int j = 0; j < S; j++) ws = ws + w[j];
+#pragma unroll
+      for (int m = 0; m < S; m++) {
+        wa[m] = R(0);
+#pragma unroll
+        for (int j = m + 1; j < S; j++)
+          if (Tab::a(j, m) != 0.0) wa[m] = wa[m] + w[j] * R(Tab::a(j, m));
+      }
+#pragma unroll
+      for (int i = 0; i < DH; i++) {
+        T ax = T(R(0)), av = T(R(0));
+#pragma unroll
+        for (int m = 0; m < S; m++) {
+          ax = ax + wa[m] * k[m][DH + i];
+          av = av + w[m] * k[m][DH + i];
+        }
+        hi[i] = y[i];
+        lo[i] = ylo[i] + hr * (ws * y[DH + i] + hr * ax);
+        hi[DH + i] = y[DH + i];
+        lo[DH + i] = ylo[DH + i] + hr * av;
+      }
+    } else if constexpr (Tab::DENSE_POLY) {
       R w[S];
       Tab::dense(sig, w);
       const R hr = R(hh);
@@ -763,6 +809,10 @@ struct Traj {
   // attempt() and replay_step(), so that the reverse pass's replay of a checkpoint segment
   // reproduces the forward's states bit for bit.
   __device__ __forceinline__ void step_core(R hr, T (*k)[D], T* ynew, R* ynlo) const {
+    if constexpr (RKN) {
+      step_core_nystrom(hr, k, ynew, ynlo);
+      return;
+    }
     T Ylast[D];
 #pragma unroll
     for (int i = 0; i < D; i++) k[0][i] = k1[i];
@@ -801,6 +851,52 @@ struct Traj {
           ynew[i] = fmadd(h, acc, y[i]);
         }
       }
+    }
+  }
+  // The stage position X_j = x + c'_j h v + h^2 sum_m (A^2)_jm a_m of the Nystrom form (c'_j the
+  // row sum of A; hv = h v); the stage's velocity slot keeps v, which the acceleration does not read.
+  __device__ __forceinline__ void nystrom_stage(int j, R hr2, const T* hv, T (*k)[D], T* Yj) const {
+#pragma unroll
+    for (int i = 0; i < DH; i++) {
+      T xs = y[i];
+      if (j >= 2) {
+        T acc = T(R(0));
+#pragma unroll
+        for (int m = 0; m < j - 1; m++)
+          if (NY::aa(j, m) != 0.0) acc = fmadd(R(NY::aa(j, m)), k[m][DH + i], acc);
+        xs = fmadd(hr2, acc, xs);
+      }
+      Yj[i] = fmadd(R(NY::row(j)), hv[i], xs);
+      Yj[DH + i] = y[DH + i];
+    }
+  }
+  // step_core in Nystrom form: the stages of the general form with k[j] = f(X_j), of which only the
+  // accelerations a_j are used; the new state x + h (v + h sum_m (bA)_m a_m), v + h sum_j b_j a_j,
+  // each an increment of the compensated pair as in the general form
+  __device__ __forceinline__ void step_core_nystrom(R hr, T (*k)[D], T* ynew, R* ynlo) const {
+    const R hr2 = hr * hr;
+    T hv[DH];
+#pragma unroll
+    for (int i = 0; i < DH; i++) hv[i] = hr * y[DH + i];
+#pragma unroll
+    for (int i = 0; i < D; i++) k[0][i] = k1[i];
+#pragma unroll
+    for (int j = 1; j < S; j++) {
+      T Yj[D];
+      nystrom_stage(j, hr2, hv, k, Yj);
+      if constexpr (DF) Sys::f((R(th) + R(tl)) + R(Tab::c(j)) * hr, Yj, p, k[j]);
+      else Sys::f(stage_time(t + Tab::c(j) * h), Yj, p, k[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < DH; i++) {
+      T ax = T(R(0)), av = T(R(0));
+#pragma unroll
+      for (int m = 0; m < S; m++) {
+        if (NY::ba(m) != 0.0) ax = fmadd(R(NY::ba(m)), k[m][DH + i], ax);
+        if (Tab::b(m) != 0.0) av = fmadd(R(Tab::b(m)), k[m][DH + i], av);
+      }
+      state_update(y[i], fmadd(hr, fmadd(hr, ax, y[DH + i]), T(ylo[i])), ynew[i], ynlo[i]);
+      state_update(y[DH + i], fmadd(hr, av, T(ylo[DH + i])), ynew[DH + i], ynlo[DH + i]);
     }
   }
   // the state after an accepted step (FSAL pairs: its first stage is the step's last one)
@@ -983,9 +1079,17 @@ struct Traj {
 #pragma unroll
       for (int i = 0; i < D; i++) {
         R acc = R(0);
+        if (RKN && i < DH) {
+          // Nystrom form: the position error h sum_j bt_j V_j = h^2 sum_m (bt A)_m a_m (sum_j bt_j = 0)
 #pragma unroll
-        for (int j = 0; j < S; j++)
-          if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * val(k[j][i]);
+          for (int m = 0; m < S; m++)
+            if (NY::bta(m) != 0.0) acc = acc + R(NY::bta(m)) * val(k[m][DH + i]);
+          acc = hr * acc;
+        } else {
+#pragma unroll
+          for (int j = 0; j < S; j++)
+            if (Tab::bt(j) != 0.0) acc = acc + R(Tab::bt(j)) * val(k[j][i]);
+        }
         const R e = hr * acc;
         const R a = fabsf(val(y[i])), b = fabsf(val(ynew[i]));
         const R sc = atolf + rtolf * (a > b ? a : b);

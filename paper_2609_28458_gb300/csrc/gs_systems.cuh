@@ -61,6 +61,7 @@ template <class R>
 struct Isochrone {
   static constexpr int D = 6, P = 0;
   static constexpr bool AUTONOMOUS = true;
+  static constexpr bool SECOND_ORDER = true;  // y = (x, v), f = (v, a(x))
   __device__ static void f(R, const R* y, const R*, R* out) {
     const R u = R(1) + (y[0] * y[0] + y[1] * y[1] + y[2] * y[2]);
     const R is = grsqrt(u);            // 1/s
@@ -102,6 +103,7 @@ template <class R>
 struct MilkyWay {
   static constexpr int D = 6, P = 4, PP = 6;  // prepared: p[0..2] = G M, p[4] = 1/q^2, p[5] = 1/q^3
   static constexpr bool AUTONOMOUS = true;
+  static constexpr bool SECOND_ORDER = true;  // y = (x, v), f = (v, a(x))
   __device__ static void prep(R* p) {
     const R G = R(kGmw);
     p[0] = G * p[0];
@@ -237,6 +239,7 @@ template <class R>
 struct LogHalo {
   static constexpr int D = 6, P = 3, PP = 5;  // p[3] = 1/q^2, p[4] = 1/q^3
   static constexpr bool AUTONOMOUS = true;
+  static constexpr bool SECOND_ORDER = true;  // y = (x, v), f = (v, a(x))
   __device__ static void prep(R* p) {
     const R iq = grcp(p[2]);
     p[3] = iq * iq;
@@ -576,6 +579,12 @@ __device__ __forceinline__ void prep_params(Rp* p) {
 // float4s per stage that a system's f_save leaves for its vjp_saved (0: the system has neither)
 template <class Sys, class = void> struct SaveQ { static constexpr int value = 0; };
 template <class Sys> struct SaveQ<Sys, std::void_t<decltype(Sys::kSaveQ)>> { static constexpr int value = Sys::kSaveQ; };
+// second-order systems: y = (x, v) with f(y) = (v, a(x)), the acceleration independent of v (and of
+// t); the FP32 modes take their stages in Nystrom form (gs_tableaux.cuh, Nystrom)
+template <class Sys, class = void> struct SecondOrder { static constexpr bool value = false; };
+template <class Sys> struct SecondOrder<Sys, std::void_t<decltype(Sys::SECOND_ORDER)>> {
+  static constexpr bool value = Sys::SECOND_ORDER;
+};
 // The factor that turns a system's parameter cotangent, as its vjp returns it, into the cotangent of
 // the parameter itself: 1, except where prep() rescales a parameter and vjp differentiates by the
 // prepared value (the Milky-Way masses, prepared as G M). Callers apply it once per trajectory.

@@ -142,4 +142,35 @@ struct Vern7 {
   __device__ static void dense(R, R*) {}
 };
 
+// The coefficients of a pair's stages in Nystrom form, for second-order systems y = (x, v),
+// f = (v, a(x)). With V_l = v + h sum_m a_lm a_m, the stage positions are
+//   X_j = x + h (sum_l a_jl) v + h^2 sum_m (A^2)_jm a_m,
+// the new position x + h (sum_j b_j) v + h^2 sum_m (b A)_m a_m and the position error
+// h (sum_j bt_j) v + h^2 sum_m (bt A)_m a_m, where sum_j b_j = 1 and sum_j bt_j = 0. A is strictly
+// lower triangular, so (A^2)_jm vanishes for m >= j - 1. The same stages as the general form, with
+// stage sums over three components instead of six.
+template <class Tab>
+struct Nystrom {
+  __host__ __device__ static constexpr double row(int j) {  // sum_l a_jl
+    double s = 0.0;
+    for (int l = 0; l < j; l++) s += Tab::a(j, l);
+    return s;
+  }
+  __host__ __device__ static constexpr double aa(int j, int m) {  // (A^2)_jm
+    double s = 0.0;
+    for (int l = m + 1; l < j; l++) s += Tab::a(j, l) * Tab::a(l, m);
+    return s;
+  }
+  __host__ __device__ static constexpr double ba(int m) {  // (b A)_m
+    double s = 0.0;
+    for (int j = m + 1; j < Tab::S; j++) s += Tab::b(j) * Tab::a(j, m);
+    return s;
+  }
+  __host__ __device__ static constexpr double bta(int m) {  // (bt A)_m
+    double s = 0.0;
+    for (int j = m + 1; j < Tab::S; j++) s += Tab::bt(j) * Tab::a(j, m);
+    return s;
+  }
+};
+
 }  // namespace gs
