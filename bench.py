@@ -122,8 +122,8 @@ def att_flops(prec):
 # case (a tape of a few GB; profiles/), divided by that launch's accepted steps; the traffic is
 # proportional to the accepted steps, so it scales to the full launch. None: not captured for that
 # kernel, or the kernel changed since.
-FWD_DRAM_BYTES_PER_STEP = {"fp32": 58.3, "fp32df": 59.3, "fp64": None}
-REV_DRAM_BYTES_PER_STEP = {"fp32": 54.9, "fp32df": 54.9, "fp64": None}
+FWD_DRAM_BYTES_PER_STEP = {"fp32": 58.5, "fp32df": 61.7, "fp64": None}
+REV_DRAM_BYTES_PER_STEP = {"fp32": 55.0, "fp32df": 54.9, "fp64": None}
 # Fallback peaks when the probe cannot run: FP32 from unit counts and clock (152 SMs x 128 FP32
 # lanes x 2 flop x 2.07 GHz); FP64 the nominal GB300 rate
 PEAK_FP32_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12
