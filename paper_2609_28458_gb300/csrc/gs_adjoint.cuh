@@ -30,6 +30,12 @@ struct Adjoint {
   using Sys = typename T::Sys;
   static constexpr int D = T::D, NP = T::NP, S = Tab::S, NPA = T::NPA;
   static constexpr int Q = SaveQ<Sys>::value;
+  // Nystrom form (the forward's stages of second-order systems in the FP32 modes): the stage
+  // cotangents are those of the accelerations, abar_j = kbar_j's velocity part, over DH components
+  static constexpr bool RKN = T::RKN;
+  static constexpr int DH = T::DH;
+  static constexpr int KD = RKN ? DH : D;
+  using NY = Nystrom<Tab>;
   static_assert(!SLAB || (Q > 0 && F32 && !DD), "saved stage factors need an FP32 mode and f_save");
   static_assert(!CK || !DD, "checkpoint strides above 1 are not built for the df64 mode");
   static constexpr int kSegMax = kChunk;  // largest checkpoint stride
@@ -86,6 +92,76 @@ struct Adjoint {
     }
 #pragma unroll
     for (int q = 0; q < NP; q++) pacc.add(q, gsum[q]);
+  }
+
+  // reverse_stages in Nystrom form. With kbar_j = (xbar_j, abar_j) the general sweep's cotangents
+  // of k_j = (V_j, a_j), substituting xbar_j = init + h sum_i a_ij Xbar_i leaves
+  //   abar_l = (its initial value) + h^2 sum_i (A^2)_il Xbar_i,   Xbar_i = J_a(X_i)^T abar_i,
+  //   ybar_x += sum_i Xbar_i,   ybar_v += h sum_i c'_i Xbar_i,
+  // the initial values (b-terms and dense outputs) already carrying h A^T of their position parts
+  // (step(), inject()). The same cotangents as the general sweep, over three components.
+  template <bool USE_SLAB = false>
+  __device__ static void reverse_stages_nystrom(const T& tr, double tt, double hh, R (*Y)[D], R (*abar)[KD], int jmax,
+                                                R* ybar, PAcc& pacc, unsigned sl = 0, unsigned st = 0) {
+    const R hr = T::cvt(hh);
+    const R hr2 = hr * hr;
+    R gsum[NPA];
+#pragma unroll
+    for (int q = 0; q < NPA; q++) gsum[q] = R(0);
+#pragma unroll
+    for (int j = S - 1; j >= 0; j--) {
+      if (j < jmax) {
+        R w[D], gy[D], gp[NPA];
+#pragma unroll
+        for (int i = 0; i < DH; i++) { w[i] = R(0); w[DH + i] = abar[j][i]; }
+        if constexpr (USE_SLAB) Sys::vjp_saved(tr.stage_time(tt + Tab::c(j) * hh), Y[j], tr.p, w, gy, gp,
+                                               sl + unsigned(j * Q) * st, st);
+        else Sys::vjp(tr.stage_time(tt + Tab::c(j) * hh), Y[j], tr.p, w, gy, gp);
+        const R hc = hr * R(NY::row(j));
+#pragma unroll
+        for (int i = 0; i < DH; i++) {
+          ybar[i] += gy[i];
+          ybar[DH + i] += hc * gy[i];
+        }
+#pragma unroll
+        for (int q = 0; q < NP; q++) gsum[q] += gp[q];
+#pragma unroll
+        for (int l = 0; l < j - 1; l++) {
+          if (NY::aa(j, l) != 0.0) {
+            const R c = hr2 * R(NY::aa(j, l));
+#pragma unroll
+            for (int i = 0; i < DH; i++) abar[l][i] += c * gy[i];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NP; q++) pacc.add(q, gsum[q]);
+  }
+  // the b-terms of the new state's cotangent ybar, before the stage sweep: general form
+  // kbar_j += h b_j ybar; Nystrom form abar_j += h b_j ybar_v + h^2 (bA)_j ybar_x and
+  // ybar_v += h ybar_x (x+ = x + h v + ...; sum_j b_j = 1)
+  __device__ static void seed_b(R hr, R (*kbar)[KD], R* ybar) {
+    if constexpr (RKN) {
+      const R hr2 = hr * hr;
+#pragma unroll
+      for (int j = 0; j < S; j++)
+#pragma unroll
+        for (int i = 0; i < DH; i++) {
+          R v = kbar[j][i];
+          if (Tab::b(j) != 0.0) v += hr * R(Tab::b(j)) * ybar[DH + i];
+          if (NY::ba(j) != 0.0) v += hr2 * R(NY::ba(j)) * ybar[i];
+          kbar[j][i] = v;
+        }
+#pragma unroll
+      for (int i = 0; i < DH; i++) ybar[DH + i] += hr * ybar[i];
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; j++)
+        if (Tab::b(j) != 0.0)
+#pragma unroll
+          for (int i = 0; i < D; i++) kbar[j][i] += hr * R(Tab::b(j)) * ybar[i];
+    }
   }
 
   struct SlotView {
@@ -420,12 +496,12 @@ struct Adjoint {
         if (!(cur.last && save_at(pb, n, q) == t1)) { dense_here = true; break; }
       }
     }
-    R k[S][D], Y[S][D], kbar[S][D];
+    R k[S][D], Y[S][D], kbar[S][KD];
     tr.template stages<SLAB>(cur.t, cur.h, k, Y, dense_here ? S : Tab::NREV, sl, st);
 #pragma unroll
     for (int j = 0; j < S; j++)
 #pragma unroll
-      for (int i = 0; i < D; i++) kbar[j][i] = R(0);
+      for (int i = 0; i < KD; i++) kbar[j][i] = R(0);
     R ydir[D];
 #pragma unroll
     for (int i = 0; i < D; i++) ydir[i] = R(0);
@@ -437,14 +513,13 @@ struct Adjoint {
       inject(pb, cur, save_at(pb, n, kk), k, kbar, ydir, used_last_stage, hr);
       kk--;
     }
-#pragma unroll
-    for (int j = 0; j < S; j++)
-      if (Tab::b(j) != 0.0)
-#pragma unroll
-        for (int i = 0; i < D; i++) kbar[j][i] += hr * R(Tab::b(j)) * ybar[i];
+    seed_b(hr, kbar, ybar);
 #pragma unroll
     for (int i = 0; i < D; i++) ybar[i] += ydir[i];
-    reverse_stages<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
+    if constexpr (RKN)
+      reverse_stages_nystrom<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
+    else
+      reverse_stages<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
     if (o == 0 && a > 0) {
       chunk = prev_chunk(pb, chunk);
       if (chunk < 0 || chunk >= pb.tape.pool_chunks) {  // as in init(): not this tape's layout
@@ -461,7 +536,7 @@ struct Adjoint {
   // The cotangent W[kk] of output time sv, emitted by the step cur: directly on the new state for
   // an output at t1 after the last step, else through the dense-output weights (Tsit5, Dopri5) or
   // a shortened step (Verner 7).
-  __device__ void inject(const Problem& pb, const SlotView& cur, double sv, R (*k)[D], R (*kbar)[D], R* ydir,
+  __device__ void inject(const Problem& pb, const SlotView& cur, double sv, R (*k)[D], R (*kbar)[KD], R* ydir,
                          bool& used_last_stage, R hr) {
     R w[D];
 #pragma unroll
@@ -476,13 +551,36 @@ struct Adjoint {
       // y(t_k) = y + h sum_j b_j(sig) k_j
       R wd[S];
       Tab::dense(sig, wd);
+      if constexpr (RKN) {
+        // Nystrom form: abar_l += h wd_l w_v + h^2 (wd A)_l w_x; the position part also reaches v
+        // through x(t_k) = x + h (sum_j wd_j) v + ...
+        const R hr2 = hr * hr;
+        R ws = R(0);
 #pragma unroll
-      for (int j = 0; j < S; j++)
+        for (int j = 0; j < S; j++) ws = ws + wd[j];
 #pragma unroll
-        for (int i = 0; i < D; i++) kbar[j][i] += hr * wd[j] * w[i];
+        for (int l = 0; l < S; l++) {
+          R wa = R(0);
+#pragma unroll
+          for (int j = l + 1; j < S; j++)
+            if (Tab::a(j, l) != 0.0) wa = wa + wd[j] * R(Tab::a(j, l));
+#pragma unroll
+          for (int i = 0; i < DH; i++) kbar[l][i] += hr * wd[l] * w[DH + i] + hr2 * wa * w[i];
+        }
+#pragma unroll
+        for (int i = 0; i < DH; i++) {
+          ydir[i] += w[i];
+          ydir[DH + i] += w[DH + i] + hr * ws * w[i];
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < S; j++)
+#pragma unroll
+          for (int i = 0; i < D; i++) kbar[j][i] += hr * wd[j] * w[i];
+#pragma unroll
+        for (int i = 0; i < D; i++) ydir[i] += w[i];
+      }
       used_last_stage = true;
-#pragma unroll
-      for (int i = 0; i < D; i++) ydir[i] += w[i];
     } else {
       // Verner 7: y(t_k) = shortened step of length sig*h from (t, y)
       const double hs = to_f64(sig) * cur.h;
@@ -526,12 +624,12 @@ struct Adjoint {
         if (!(cur.last && sq == t1)) { dense_here = true; break; }
       }
     }
-    R k[S][D], Y[S][D], kbar[S][D];
+    R k[S][D], Y[S][D], kbar[S][KD];
     tr.template stages<SLAB>(cur.t, cur.h, k, Y, dense_here ? S : Tab::NREV, sl, st);
 #pragma unroll
     for (int j = 0; j < S; j++)
 #pragma unroll
-      for (int i = 0; i < D; i++) kbar[j][i] = R(0);
+      for (int i = 0; i < KD; i++) kbar[j][i] = R(0);
     // cotangents reaching the step's start state directly (identity term of an output inside it)
     R ydir[D];
 #pragma unroll
@@ -545,51 +643,17 @@ struct Adjoint {
       if (sv == t0) break;
       if (!inside(cur, sv)) break;
       if (a > 0 && inside(decode(nraw), sv)) break;
-      R w[D];
-#pragma unroll
-      for (int i = 0; i < D; i++) w[i] = R(W[kk * D + i]);
-      if (cur.last && sv == t1) {
-#pragma unroll
-        for (int i = 0; i < D; i++) ybar[i] += w[i];  // y(t1) is the new state itself
-      } else {
-        const R sig = sigma(cur, sv);
-        if constexpr (Tab::DENSE_POLY) {
-          // y(t_k) = y + h sum_j b_j(sig) k_j
-          R wd[S];
-          Tab::dense(sig, wd);
-#pragma unroll
-          for (int j = 0; j < S; j++)
-#pragma unroll
-            for (int i = 0; i < D; i++) kbar[j][i] += hr * wd[j] * w[i];
-          used_last_stage = true;
-#pragma unroll
-          for (int i = 0; i < D; i++) ydir[i] += w[i];
-        } else {
-          // Verner 7: y(t_k) = shortened step of length sig*h from (t, y)
-          const double hs = to_f64(sig) * cur.h;
-          R ks[S][D], Ys[S][D], kbs[S][D];
-          tr.stages(cur.t, hs, ks, Ys, Tab::NREV);
-          const R hsr = R(hs);
-#pragma unroll
-          for (int j = 0; j < S; j++)
-#pragma unroll
-            for (int i = 0; i < D; i++) kbs[j][i] = (j < Tab::NREV) ? hsr * R(Tab::b(j)) * w[i] : R(0);
-#pragma unroll
-          for (int i = 0; i < D; i++) ydir[i] += w[i];
-          reverse_stages(tr, cur.t, hs, Ys, kbs, Tab::NREV, ydir, pacc);
-        }
-      }
+      inject(pb, cur, sv, k, kbar, ydir, used_last_stage, hr);
       kk--;
     }
     // the step itself: kbar_j += h b_j ybar, then the stages in reverse
-#pragma unroll
-    for (int j = 0; j < S; j++)
-      if (Tab::b(j) != 0.0)
-#pragma unroll
-        for (int i = 0; i < D; i++) kbar[j][i] += hr * R(Tab::b(j)) * ybar[i];
+    seed_b(hr, kbar, ybar);
 #pragma unroll
     for (int i = 0; i < D; i++) ybar[i] += ydir[i];
-    reverse_stages<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
+    if constexpr (RKN)
+      reverse_stages_nystrom<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
+    else
+      reverse_stages<SLAB>(tr, cur.t, cur.h, Y, kbar, used_last_stage ? S : Tab::NREV, ybar, pacc, sl, st);
     chunk = pchunk;
     a -= 1;
     if (a < 0) finish(pb);
