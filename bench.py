@@ -68,13 +68,15 @@ ORACLE_RTOL = 1e-13  # the converged reference (Appendix A: the paper's referenc
 # the stage positions from the coefficients (A^2)_jm (zero for m >= j - 1) and the row sums of A,
 # over the d/2 position components only, and the position error from ((b - bhat) A)_m. Counted the
 # same way, a forward attempt is (S - 1) f + d (nnz A^2 + S - 1) + d (nnz((b - bhat) A) + nnz(b - bhat))
-# + 40 = 468 + 6*(15+6) + 6*(6+7) + 40 = 712, and a reversed step recomputes its stages with
-# d (nnz A^2 among the 6 + 2*5) = 6*(10+10) instead of 2d (15 + 5): 2010.
+# + 40 = 468 + 6*(15+6) + 6*(6+7) + 40 = 712. A reversed step recomputes its stages with
+# d (nnz A^2 among the 6 + 2*5) = 6*(10+10) instead of 2d (15 + 5), and its cotangent algebra, over
+# the accelerations' cotangents, is d (nnz A^2 among the 6 + 6 c' terms + nnz b + nnz bA) =
+# 6*(10+6+6+5) instead of 2d (15 + 6): 1920.
 F_RHS_MW = 78
 F_ATT_FWD = 6 * F_RHS_MW + 2 * 6 * (21 + 7) + 40
 F_STEP_REV = 6 * F_RHS_MW + 2 * 6 * (15 + 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
 F_ATT_FWD_NY = 6 * F_RHS_MW + 6 * (15 + 6) + 6 * (6 + 7) + 40
-F_STEP_REV_NY = 6 * F_RHS_MW + 6 * (10 + 2 * 5) + 6 * int(2.5 * F_RHS_MW) + 2 * 6 * (15 + 6)
+F_STEP_REV_NY = 6 * F_RHS_MW + 6 * (10 + 2 * 5) + 6 * int(2.5 * F_RHS_MW) + 6 * (10 + 6 + 6 + 5)
 F64_ATT_SPLIT = 2 * 6 + 5
 # Forward flops of the other workloads, the same count for any system and tableau: per attempt
 # (S - 1) f + 2d (nnz A + nnz(b - bhat)) + 40, plus 2d nnz b for the new state and one f per accepted
@@ -84,8 +86,8 @@ F64_ATT_SPLIT = 2 * 6 + 5
 F_RHS = {"mw": 78, "precession": 172, "isochrone": 14, "loghalo": 30, "quintessence": 40}
 TABLEAU_NNZ = {"tsit5": (7, True, 21, 6, 7), "dopri5": (7, True, 20, 5, 6), "vern7": (10, False, 36, 7, 8)}
 # Nystrom form (FP32 modes, second-order systems, the 7-stage FSAL pairs): nnz A^2 over stages 2..S,
-# nnz A^2 over the first 6 stages, nnz((b - bhat) A)
-NYSTROM_NNZ = {"tsit5": (15, 10, 6), "dopri5": (14, 10, 5)}
+# nnz A^2 over the first 6 stages, nnz((b - bhat) A), nnz(b A)
+NYSTROM_NNZ = {"tsit5": (15, 10, 6, 5), "dopri5": (14, 10, 5, 4)}
 SECOND_ORDER = ("mw", "isochrone", "loghalo")
 
 
@@ -97,19 +99,24 @@ def forward_flops(system, method, d, attempts, accepted, prec="fp64"):
     S, fsal, n_a, n_b, n_e = TABLEAU_NNZ[method]
     f = F_RHS[system]
     if nystrom(system, method, prec):
-        n_aa, _, n_ea = NYSTROM_NNZ[method]
+        n_aa, _, n_ea, _ = NYSTROM_NNZ[method]
         return attempts * ((S - 1) * f + d * (n_aa + S - 1) + d * (n_ea + n_e) + 40)
     per_attempt = (S - 1) * f + 2 * d * (n_a + (0 if fsal else n_b) + n_e) + 40
     return attempts * per_attempt + (0 if fsal else accepted * f)
 
 
 def reverse_flops(system, method, d, accepted, prec="fp64"):
-    """Per accepted step: the stages recomputed (S - 1 f + 2d nnz A; Nystrom form: d (nnz A^2 among
-    the first 6 stages + 2*5)), S VJPs at 2.5 f, and the cotangent algebra 2d (nnz A + nnz b)."""
+    """Per accepted step: the stages recomputed (S - 1 f + 2d nnz A), S VJPs at 2.5 f, and the
+    cotangent algebra 2d (nnz A + nnz b); in Nystrom form the recomputation d (nnz A^2 among the
+    first 6 stages + 2*5) and the algebra d (nnz A^2 among them + 6 + nnz b + nnz bA)."""
     S, fsal, n_a, n_b, n_e = TABLEAU_NNZ[method]
     f = F_RHS[system]
-    recompute = d * (NYSTROM_NNZ[method][1] + 10) if nystrom(system, method, prec) else 2 * d * n_a
-    return accepted * ((S - 1) * f + recompute + S * int(2.5 * f) + 2 * d * (n_a + n_b))
+    if nystrom(system, method, prec):
+        _, n_aa6, _, n_ba = NYSTROM_NNZ[method]
+        recompute, algebra = d * (n_aa6 + 10), d * (n_aa6 + 6 + n_b + n_ba)
+    else:
+        recompute, algebra = 2 * d * n_a, 2 * d * (n_a + n_b)
+    return accepted * ((S - 1) * f + recompute + S * int(2.5 * f) + algebra)
 
 
 def att_flops(prec):
@@ -123,7 +130,7 @@ def att_flops(prec):
 # proportional to the accepted steps, so it scales to the full launch. None: not captured for that
 # kernel, or the kernel changed since.
 FWD_DRAM_BYTES_PER_STEP = {"fp32": 58.5, "fp32df": 61.7, "fp64": None}
-REV_DRAM_BYTES_PER_STEP = {"fp32": 55.0, "fp32df": 54.9, "fp64": None}
+REV_DRAM_BYTES_PER_STEP = {"fp32": None, "fp32df": None, "fp64": None}  # not re-taken after the Nystrom-form adjoint
 # Fallback peaks when the probe cannot run: FP32 from unit counts and clock (152 SMs x 128 FP32
 # lanes x 2 flop x 2.07 GHz); FP64 the nominal GB300 rate
 PEAK_FP32_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12

@@ -42,7 +42,7 @@ def test_nystrom_counts_match_the_oracle_tableaux():
     h^2 sum_m (A^2)_jm a_m. A is strictly lower triangular, so (A^2)_jm vanishes for m >= j - 1, and
     the counts the benchmark uses are the nonzeros of A^2 and of (b - bhat) A."""
     b = _bench()
-    for method, (n_aa, n_aa_rev, n_ea) in b.NYSTROM_NNZ.items():
+    for method, (n_aa, n_aa_rev, n_ea, n_ba) in b.NYSTROM_NNZ.items():
         T = O.tableau(method)
         A, bb, bh = np.array(T["A"]), np.array(T["b"]), np.array(T["bh"])
         AA = A @ A
@@ -52,12 +52,12 @@ def test_nystrom_counts_match_the_oracle_tableaux():
         nz = lambda x: int((np.abs(x) > 1e-14).sum())
         assert nz(AA[1:S]) == n_aa
         assert nz(AA[1:6]) == n_aa_rev
-        assert nz((bb - bh) @ A) == n_ea
+        assert nz((bb - bh) @ A) == n_ea and nz(bb @ A) == n_ba
         # the error weights sum to zero (b and bhat both sum to one), so the position error has no v term
         assert abs((bb - bh).sum()) < 1e-15 and abs(bb.sum() - 1.0) < 1e-15
     assert b.forward_flops("mw", "tsit5", 6, 1, 1, "fp32") == b.F_ATT_FWD_NY
     assert b.reverse_flops("mw", "tsit5", 6, 1, "fp32") - b.reverse_flops("mw", "tsit5", 6, 1) == \
-        6 * (10 + 10) - 2 * 6 * 21
+        6 * (10 + 10) - 2 * 6 * 21 + 6 * (10 + 6 + 6 + 5) - 2 * 6 * (21 + 6)
     assert b.att_flops("fp64") == (b.F_ATT_FWD, b.F_STEP_REV)
     assert b.att_flops("fp32") == (b.F_ATT_FWD_NY, b.F_STEP_REV_NY)
 
