@@ -51,7 +51,10 @@ typedef enum { GS_TSIT5 = 0, GS_DOPRI5 = 1, GS_VERN7 = 2 } gs_method;
 /* GS_FP64: every operation in FP64.
  * GS_FP32_STAGES: stage and right-hand-side arithmetic in FP32, the state kept as a compensated
  *   FP32 pair, the error-norm accumulation, the time (compensated summation) and the step-size
- *   controller in FP64.
+ *   controller in FP64. For the orbit systems (isochrone, Milky Way, log halo: y = (x, v),
+ *   f = (v, a(x))) with GS_TSIT5 or GS_DOPRI5, both FP32 modes evaluate the pair's stages, dense
+ *   output and reverse sweep in Nystrom form: the same stages, with sums over the positions only
+ *   (A^2 and the row sums of A), and no difference of velocity-sized terms in the position error.
  * GS_FP32_DF: as GS_FP32_STAGES, but the time is an unevaluated FP32 pair (>= 48 significant bits,
  *   advanced error-free), the step length is the FP32 number the stages use, and the norm
  *   accumulation and controller run in FP32: the attempt loop issues no FP64 instruction.
@@ -188,10 +191,11 @@ int gs_solve(int32_t system, int64_t N, const double* y0, const double* params, 
  *  int32 output attribution emit[N, K] (the accepted step that produced each output), then chunks;
  *  a trajectory with n accepted steps uses ceil(n / 32) chunks. A chunk is a 16-byte header holding
  *  the previous chunk's index, then
- *  - stride 1: 32 slots; slot = roundup16(state) + tail: GS_FP64 state 8 d bytes (FP64), tail 32
- *    (t, tc, h, flag as FP64); GS_FP32_STAGES state 4 d (the FP32 high part, from which the stages
- *    are recomputed), tail 32; GS_FP32_DF state 4 d, tail 16 (time pair, h, flag as FP32); GS_DF64
- *    state 8 d (df64 pairs), tail 16;
+ *  - stride 1: 32 slots. GS_FP64: the state (8 d bytes), GS_FP32_STAGES: its FP32 high part (4 d
+ *    bytes, from which the stages are recomputed); then, from the next 8-byte boundary, t, tc and h
+ *    as FP64 (h negative for the last, clipped step), the slot padded to 16 bytes:
+ *    roundup16(roundup8(state) + 24), 48 bytes for six FP32 components. GS_FP32_DF: roundup16(4 d)
+ *    + 16 (time pair, h, flag as FP32); GS_DF64: roundup16(8 d) + 16 (df64 pairs, then as GS_FP32_DF);
  *  - stride S > 1: the 32 step lengths (FP64; FP32 in GS_FP32_DF; the last, clipped step negative),
  *    then 32 / S checkpoints of roundup16(state) + 16 bytes: GS_FP64 state = y and the first stage
  *    (16 d bytes), the FP32 modes its high part, low part and first stage (12 d bytes); then the
