@@ -30,7 +30,10 @@ struct LaunchCfg {
 // the 3 Gyr Milky-Way ensemble: with the stages in Nystrom form, forward with tape 29.1 ms against
 // 33.4 ms at 4 blocks; in the general form 4 blocks had been faster, 28.1 against 30.7 ms forward
 // alone, and 6 blocks 42% slower), the FP64-control forward 4 (115 registers; 5 blocks: 35.5 against
-// 35.3 ms), the FP32 reverse 3 (<= 168; 2 blocks is 15% slower, 4 blocks 5%). The FP64 forward of the 9-component
+// 35.3 ms), the FP32 reverse 4 (128 registers: with its stage sweep in Nystrom form, 31.1 against
+// 31.6 ms at 3 blocks; the general form had spilled there and was 5% slower, 2 blocks 15%), the
+// checkpointed FP32 reverse 3 (<= 168: its segment replay keeps the register budget it was verified
+// with). The FP64 forward of the 9-component
 // precession state 4 blocks (16 warps per SM at 128 registers, against 8 at the compiler's 255: the
 // FP64 pipe gets more warps to overlap; 10^6 Verner 7 solves 243.9 -> 222.5 ms despite spilling, 3
 // blocks 229.9 ms). Other FP64 and Verner 7 kernels keep the compiler's choice.
@@ -41,7 +44,10 @@ struct LaunchCfg {
 #define GS_FWD_BLOCKS_FP32 4
 #endif
 #ifndef GS_REV_BLOCKS_FP32
-#define GS_REV_BLOCKS_FP32 3
+#define GS_REV_BLOCKS_FP32 4
+#endif
+#ifndef GS_REV_CKPT_BLOCKS_FP32
+#define GS_REV_CKPT_BLOCKS_FP32 3
 #endif
 #ifndef GS_FWD_BLOCKS_FP64_D9
 #define GS_FWD_BLOCKS_FP64_D9 4
@@ -53,6 +59,7 @@ struct Occupancy {
                              : (PM == 1 && small) ? GS_FWD_BLOCKS_FP32
                              : (PM == 0 && SysT<float>::D == 9 && MT == 0) ? GS_FWD_BLOCKS_FP64_D9 : 1;
   static constexpr int rev = ((PM == 1 || PM == 2) && small) ? GS_REV_BLOCKS_FP32 : 1;
+  static constexpr int revck = ((PM == 1 || PM == 2) && small) ? GS_REV_CKPT_BLOCKS_FP32 : 1;
 };
 
 template <template <class> class SysT, class Tab, int PM>
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_revers
 // replaying together and reversing together; only a trajectory's first (newest, partial) segment
 // leaves a lane idle for part of a round. Lanes are refilled between rounds.
 template <template <class> class SysT, class Tab, int PM>
-__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::rev)) k_reverse_ckpt(const Problem pb) {
+__global__ void __launch_bounds__(128, (Occupancy<SysT, Tab, PM>::revck)) k_reverse_ckpt(const Problem pb) {
   constexpr bool SLAB = RevSlab<SysT, Tab, PM>::on;
   Adjoint<SysT, Tab, PM, SLAB, true> adj;
   if constexpr (SLAB) {
