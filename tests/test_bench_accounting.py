@@ -79,3 +79,19 @@ def test_nystrom_form_is_the_same_stages():
         assert np.allclose(X_general, X_nystrom, rtol=0, atol=1e-13)
         assert np.allclose(x + h * (bb @ V), x + h * v + h * h * ((bb @ A) @ acc), rtol=0, atol=1e-13)
         assert np.allclose(h * ((bb - bh) @ V), h * h * (((bb - bh) @ A) @ acc), rtol=0, atol=1e-13)
+
+
+def test_nystrom_systems_match_the_kernels():
+    """bench.py counts Nystrom-form work for exactly the systems the kernels mark second-order
+    (gs_systems.cuh, SECOND_ORDER) and the pairs they take in that form (7-stage FSAL)."""
+    import re
+    src = open(os.path.join(ROOT, "paper_2609_28458_gb300", "csrc", "gs_systems.cuh")).read()
+    marked = set()
+    for m in re.finditer(r"struct (\w+) \{(.*?)\n\};", src, re.S):
+        if "SECOND_ORDER = true" in m.group(2):
+            marked.add(m.group(1))
+    names = {"Isochrone": "isochrone", "MilkyWay": "mw", "LogHalo": "loghalo"}
+    assert {names[m] for m in marked} == set(_bench().SECOND_ORDER)
+    b = _bench()
+    for method, (S, fsal, *_rest) in b.TABLEAU_NNZ.items():
+        assert (method in b.NYSTROM_NNZ) == (fsal and S == 7)
